@@ -1,0 +1,348 @@
+"""Benchmark: pair interactions per second, forward + backward.
+
+Workload (default): d = 3, N = 2^20 points uniform in the periodic unit cube,
+r = 0.0197 (~33.6 neighbours mean), truncated Lennard-Jones (sigma = 0.01,
+eps = 1).  One step = cell-list rebuild + energy forward + adjoint (forces),
+all through the library's C ABI.  The metric counts accepted ordered pairs
+(sum over particles of the neighbour count) per second of the step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent replica of the workload
+(weak scaling, no data-path collective); value = all ranks' pairs / the
+slowest rank's time.  ``--impl reference`` times the CPU oracle (the
+reference arm of this build) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pair interactions/s fwd+bwd (3-D LJ, N=2^20, r=0.0197)"
+UNIT = "pairs/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# Algorithmic FP32 operations: per candidate pair the predicate (3 sub, 3 mul,
+# 2 add, 1 compare); per accepted pair the LJ adjoint term (1 reciprocal,
+# 3 mul for (sig/d)^6, 3 for the coefficient, 2 for (g_i + g_j), 3 FMA).
+OPS_PER_CANDIDATE = 9
+OPS_PER_PAIR_LJ_BWD = 12
+OPS_PER_PAIR_LJ_FWD = 7
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _stencil_sum_axis(f, axis, periodic):
+    """sum over the distinct stencil neighbours {c-1, c, c+1} along one axis."""
+    n = f.shape[axis]
+    if periodic:
+        if n == 1:
+            return f.copy()
+        if n == 2:
+            return np.broadcast_to(f.sum(axis=axis, keepdims=True), f.shape).copy()
+        return f + np.roll(f, 1, axis=axis) + np.roll(f, -1, axis=axis)
+    out = f.copy()
+    sl = [slice(None)] * f.ndim
+    if n > 1:
+        lo_, hi_ = list(sl), list(sl)
+        lo_[axis], hi_[axis] = slice(0, n - 1), slice(1, n)
+        out[tuple(lo_)] += f[tuple(hi_)]
+        out[tuple(hi_)] += f[tuple(lo_)]
+    return out
+
+
+def candidates_from_cells(start, ncell, periodic, dim):
+    """Exact candidate count sum_i sum_{c in stencil(cell i)} n_c from the
+    cell histogram (measurement only; the stencil is a product of per-axis
+    neighbour sets, so the box sum is separable)."""
+    shape = (ncell[2], ncell[1], ncell[0]) if dim == 3 else (ncell[1], ncell[0])
+    counts = np.diff(start.astype(np.int64)).reshape(shape)
+    s = counts
+    for k in range(dim):
+        s = _stencil_sum_axis(s, counts.ndim - 1 - k, periodic[k])
+    return int((counts * s).sum())
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1704_08907_gb300 as ab
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.c2(seed_offset=rank)
+    n = w.n
+    eps, sigma = w.params["eps"], w.params["sigma"]
+    ctx = ab.Context(local)
+    dom = ab.Domain(3, w.periodic, w.radius)
+    pos = torch.from_numpy(w.pos).to(dev)
+    E = torch.empty(n, dtype=torch.float32, device=dev)
+    F = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    etot = torch.empty((), dtype=torch.float64, device=dev)
+    ones = torch.ones(n, dtype=torch.float32, device=dev)
+    prm = ab.OpParams(eps=eps, sigma=sigma)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    # pair count (the metric's numerator) and candidate count, untimed
+    ab.ab_build(ctx, dom, pos)
+    pairs = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
+    perm, start = ab.ab_cell_export(ctx)
+    ncell, _ = ab.ab_cell_shape(ctx)
+    cands = candidates_from_cells(start.cpu().numpy().view(np.uint32), ncell, w.periodic, 3)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        ab.ab_build(ctx, dom, pos)
+        if ev is not None:
+            ev[1].record()
+        ab.ab_pair_sum(ctx, "lj", prm, out=E, energy=etot)
+        if ev is not None:
+            ev[2].record()
+        ab.ab_pair_sum_bwd(ctx, "lj", prm, None, ones, grad_pos4=F)
+        if ev is not None:
+            ev[3].record()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                         # untimed: evict L2 between steps
+        step(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    t_build = np.array([a[0].elapsed_time(a[1]) for a in evs])
+    t_fwd = np.array([a[1].elapsed_time(a[2]) for a in evs])
+    t_bwd = np.array([a[2].elapsed_time(a[3]) for a in evs])
+    t_step = t_build + t_fwd + t_bwd                       # ms, device time
+    total_ms = float(t_step.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = pairs * world * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    pos_h = torch.from_numpy(w.pos).pin_memory()
+    F_h = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    e_h = torch.empty((), dtype=torch.float64).pin_memory()
+    pos_d = torch.empty_like(pos)
+
+    def e2e_step():
+        pos_d.copy_(pos_h, non_blocking=True)
+        ab.lj_energy_forces(ctx, dom, pos_d, eps, sigma, E=E, F=F, energy=etot, g=ones)
+        F_h.copy_(F, non_blocking=True)
+        e_h.copy_(etot, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record()
+        e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    ab.ab_sync(ctx)
+
+    pk, pk_kind = peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
+    bwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_BWD
+    bwd_s = float(np.mean(t_bwd)) * 1e-3
+    achieved = bwd_ops / bwd_s / 1e12
+    fwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_FWD
+    build_bytes = n * (16 + 4 + 4) + n * (4 + 4 + 4 + 4) + n * (4 + 4 + 4 + 16 + 4 + 16) \
+        + 8 * (int(np.prod(ncell)) + 1)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3-D uniform periodic cube, N=1048576, r=0.0197, "
+                               "Lennard-Jones sigma=0.01 eps=1: rebuild + energy + forces",
+                   "n": n, "radius": w.radius, "pairs_per_step": pairs,
+                   "candidates_per_step": cands, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,LJ>",
+                     "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"},
+        "phases_ms": {"build": float(np.mean(t_build)), "fwd": float(np.mean(t_fwd)),
+                      "bwd": float(np.mean(t_bwd))},
+        "phase_roofline": {
+            "build_hbm_gbs": build_bytes / (float(np.mean(t_build)) * 1e-3) / 1e9,
+            "build_hbm_frac": build_bytes / (float(np.mean(t_build)) * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "fwd_alu_frac": fwd_ops / (float(np.mean(t_fwd)) * 1e-3) / 1e12 / alu_peak,
+            "peak_kind": pk_kind},
+        "e2e": {"value": pairs * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16 + 8},
+        "gpu_launches": 8 * args.steps,
+        "wall_s": wall,
+    }
+    if clk:
+        out["clocks"] = clk
+    return out, w
+
+
+def oracle_sample(w, nq, seed=17):
+    """Oracle LJ energy + adjoint over nq query particles (cell list over all)."""
+    import oracle
+    box = oracle.Box(3, w.periodic, w.lo, w.hi, w.radius)
+    q = synth.query_sample(w.n, nq, seed)
+    t0 = time.perf_counter()
+    cl = oracle.CellList(box, w.pos)
+    off, idx = cl.neighbours(q)
+    oracle.pair_values("lj", box, w.pos, off, idx, q, params=w.params)
+    oracle.pair_grads("lj", box, w.pos, off, idx, np.ones(w.n), q, params=w.params)
+    dt = time.perf_counter() - t0
+    return int(off[-1]), dt, oracle.num_threads()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-queries", type=int, default=131072)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        w = synth.c2()
+        nq = args.oracle_queries
+        pairs, secs = 0, 0.0
+        for _ in range(args.warmup):
+            oracle_sample(w, max(nq // 8, 1024))
+        for _ in range(args.steps):
+            p, dt, cores = oracle_sample(w, nq)
+            pairs += p
+            secs += dt
+        v = pairs / secs
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "3-D uniform periodic cube, N=1048576, r=0.0197, "
+                                   "Lennard-Jones sigma=0.01 eps=1: rebuild + energy + forces"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"oracle cell list over all 1048576 points + LJ energy "
+                                       f"and adjoint for {nq} query particles per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out, w = run_ours(args, rank, world)
+    if rank == 0:
+        pairs, secs, cores = oracle_sample(w, args.oracle_queries)
+        out["cpu_baseline"] = {"value": pairs / secs, "unit": UNIT, "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"oracle cell list over all {w.n} points + LJ energy "
+                                         f"and adjoint for {args.oracle_queries} query particles"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,34 @@
+/*
+ * aboria_gpu_testing.h -- test hooks of the aboria_gpu library.
+ *
+ * These entry points exist so that tests can exercise device-side error
+ * paths without faulting or hanging a GPU.  They are not part of the
+ * computational API and the paper has no counterpart for them.
+ */
+#ifndef ABORIA_GPU_TESTING_H
+#define ABORIA_GPU_TESTING_H
+
+#include <stdint.h>
+
+#include "aboria_gpu.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Run the cell-offset scan (the decoupled look-back prefix scan used by
+ * ab_build) over `items` zeros on the context's scratch, with tile
+ * `skip_tile` never publishing its status, so that the next tile's bounded
+ * wait runs out after `limit_ns` nanoseconds (0 < limit_ns <= 2e9).  The
+ * kernel then records the timeout in the context's error word and finishes;
+ * the following ab_sync() returns AB_ERR_TIMEOUT and clears it.  Nothing
+ * spins without a limit and no memory outside the scratch is touched.
+ * Errors: AB_ERR_INVALID_ARG, AB_ERR_OOM, AB_ERR_CUDA. */
+ab_status ab_testing_scan_timeout(ab_ctx* ctx, int64_t items, int32_t skip_tile,
+                                  int64_t limit_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABORIA_GPU_TESTING_H */

@@ -1,0 +1,567 @@
+// C ABI entry points: argument validation, workspace management and launch
+// sequencing.  Every step of the computation runs in the kernels of
+// ab_cells.cu, ab_pairs.cu, ab_dense.cu and ab_bd.cu; this file only checks,
+// allocates and orders.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "ab_internal.cuh"
+#include "../../include/aboria_gpu_testing.h"
+
+namespace ab {
+int g_num_sms = 152;
+}
+
+struct ab_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ab::CellList cl;
+    ab::Scratch sc;
+    uint32_t* d_err = nullptr;
+    std::string last_error;
+};
+
+namespace {
+
+using ab::CellList;
+using ab::Geom;
+
+ab_status fail(ab_ctx* c, ab_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return s;
+}
+
+ab_status cuda_fail(ab_ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(c, AB_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(c, AB_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Stream-ordered growth: allocate the new buffer before freeing the old one,
+// so a failed allocation leaves the previous workspace intact.
+template <typename T>
+cudaError_t grow(T** p, size_t* cap, size_t need, cudaStream_t st) {
+    if (need <= *cap && *p) return cudaSuccess;
+    size_t want = need + need / 4 + 64;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, want * sizeof(T), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    if (*p) cudaFreeAsync(*p, st);
+    *p = (T*)q;
+    *cap = want;
+    return cudaSuccess;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    if (!a || !b || na == 0 || nb == 0) return false;
+    uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+ab_status check_domain(ab_ctx* c, const ab_domain* d) {
+    if (!d) return fail(c, AB_ERR_INVALID_ARG, "domain is NULL");
+    if (d->dim != 2 && d->dim != 3) return fail(c, AB_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", d->dim);
+    if (!(d->radius > 0.0f) || !isfinite(d->radius))
+        return fail(c, AB_ERR_INVALID_ARG, "radius must be finite and > 0");
+    for (int k = 0; k < d->dim; ++k) {
+        if (!isfinite(d->lo[k]) || !isfinite(d->hi[k]) || !(d->hi[k] > d->lo[k]))
+            return fail(c, AB_ERR_INVALID_ARG, "axis %d: need finite lo < hi", k);
+        float L = d->hi[k] - d->lo[k];
+        if (!isfinite(L)) return fail(c, AB_ERR_INVALID_ARG, "axis %d: box too large", k);
+    }
+    return AB_OK;
+}
+
+// Cell geometry (see ab_build in the header for the width rule).
+Geom make_geom(const ab_domain* d, int64_t n) {
+    Geom g{};
+    g.dim = d->dim;
+    g.r = d->radius;
+    g.r2 = d->radius * d->radius;
+    int64_t nk[3] = {1, 1, 1};
+    for (int k = 0; k < 3; ++k) {
+        g.periodic[k] = 0;
+        g.lo[k] = 0.0f;
+        g.L[k] = 1.0f;
+        g.halfL[k] = 0.5f;
+        g.inv_w[k] = 0.0f;
+    }
+    for (int k = 0; k < d->dim; ++k) {
+        g.periodic[k] = d->periodic[k] ? 1 : 0;
+        g.lo[k] = d->lo[k];
+        g.L[k] = d->hi[k] - d->lo[k];
+        g.halfL[k] = 0.5f * g.L[k];
+        const double L = (double)g.L[k];
+        const double wmin = (double)d->radius * (1.0 + 0x1p-18) + L * 0x1p-18;
+        double c = floor(L / wmin);
+        if (c < 1.0) c = 1.0;
+        if (c > (double)(1 << 21)) c = (double)(1 << 21);
+        nk[k] = (int64_t)c;
+    }
+    const int64_t cap = n * 4 > (int64_t(1) << 22) ? n * 4 : (int64_t(1) << 22);
+    for (;;) {
+        int64_t t = nk[0] * nk[1] * nk[2];
+        if (t <= cap) break;
+        for (int k = 0; k < d->dim; ++k) nk[k] = nk[k] > 1 ? nk[k] / 2 : 1;
+    }
+    g.general = 0;
+    g.n_cells = 1;
+    for (int k = 0; k < 3; ++k) {
+        g.n[k] = (int)nk[k];
+        g.n_cells *= nk[k];
+        if (k < d->dim) {
+            g.inv_w[k] = (float)((double)nk[k] / (double)g.L[k]);
+            if (g.periodic[k] && nk[k] < 5) g.general = 1;
+        }
+    }
+    return g;
+}
+
+ab_status ensure_sv(ab_ctx* c, int64_t n) {
+    cudaError_t e = grow(&c->sc.sv, &c->sc.cap_sv, (size_t)(n > 0 ? n : 1), c->stream);
+    return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "workspace (variables)");
+}
+
+ab_status ensure_partial(ab_ctx* c, size_t count) {
+    cudaError_t e = grow(&c->sc.partial, &c->sc.cap_partial, count > 0 ? count : 1, c->stream);
+    return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "workspace (partials)");
+}
+
+ab_status ensure_scan(ab_ctx* c, int64_t items) {
+    size_t tiles = ab::scan_tiles(items) + 1;
+    cudaError_t e = grow(&c->sc.scan_status, &c->sc.cap_tiles, tiles, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "workspace (scan)");
+    if (!c->sc.scan_ticket) {
+        e = cudaMallocAsync((void**)&c->sc.scan_ticket, 16, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "workspace (scan ticket)");
+    }
+    return AB_OK;
+}
+
+ab_status require_cells(ab_ctx* c) {
+    if (!c->cl.valid)
+        return fail(c, AB_ERR_STALE, "no current cell list: call ab_build after creating the "
+                                     "context or after moving the particles");
+    return AB_OK;
+}
+
+size_t out_bytes(ab_op op, int64_t n) {
+    return (op == AB_OP_EXPF || op == AB_OP_SOFT) ? (size_t)n * 16 : (size_t)n * 4;
+}
+
+}  // namespace
+
+// The library is built with -fvisibility=hidden; only the C ABI is exported.
+#pragma GCC visibility push(default)
+extern "C" {
+
+const char* ab_status_string(ab_status s) {
+    switch (s) {
+        case AB_OK: return "ok";
+        case AB_ERR_INVALID_ARG: return "invalid argument";
+        case AB_ERR_ALIAS: return "output overlaps an input";
+        case AB_ERR_STALE: return "cell list missing or stale";
+        case AB_ERR_OOM: return "out of device memory";
+        case AB_ERR_CUDA: return "CUDA error";
+        case AB_ERR_TIMEOUT: return "device-side wait timed out";
+        case AB_ERR_UNSUPPORTED: return "unsupported request";
+        case AB_ERR_CAPACITY: return "output capacity too small";
+    }
+    return "unknown status";
+}
+
+const char* ab_last_error(ab_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+ab_status ab_create(ab_ctx** out, int device, void* stream) {
+    if (!out) return AB_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return AB_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return AB_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return AB_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+        ab::g_num_sms = sms;
+    ab_ctx* c = new ab_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaMalloc((void**)&c->d_err, 16) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, 16) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return AB_ERR_OOM;
+    }
+    *out = c;
+    return AB_OK;
+}
+
+ab_status ab_destroy(ab_ctx* c) {
+    if (!c) return AB_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_id, c->cl.rank, c->cl.tmp,
+                    c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
+                    c->sc.partial, c->sc.counts};
+    for (void* b : bufs)
+        if (b) cudaFreeAsync(b, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_err);
+    cudaGetLastError();
+    delete c;
+    return AB_OK;
+}
+
+ab_status ab_set_stream(ab_ctx* c, void* stream) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    c->stream = (cudaStream_t)stream;
+    return AB_OK;
+}
+
+ab_status ab_sync(ab_ctx* c) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_sync");
+    uint32_t h = 0;
+    e = cudaMemcpy(&h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_sync (error word)");
+    if (h) {
+        cudaMemset(c->d_err, 0, sizeof(uint32_t));
+        if (h & ab::DEVERR_SCAN_TIMEOUT)
+            return fail(c, AB_ERR_TIMEOUT, "scan look-back wait exceeded its time limit");
+    }
+    return AB_OK;
+}
+
+ab_status ab_build(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos4) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = check_domain(c, dom);
+    if (s != AB_OK) return s;
+    if (n < 0 || n >= (int64_t(1) << 31) - 1) return fail(c, AB_ERR_INVALID_ARG, "n out of range");
+    if (n > 0 && (!pos4 || !aligned16(pos4)))
+        return fail(c, AB_ERR_INVALID_ARG, "pos4 must be a 16-byte aligned device pointer");
+    cudaSetDevice(c->device);
+    CellList& cl = c->cl;
+    cl.valid = false;
+    Geom g = make_geom(dom, n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    cudaError_t e;
+    if (nn > cl.cap_n || !cl.spos) {
+        // all per-particle buffers share one capacity
+        const size_t want = nn + nn / 4 + 64;
+        void* fresh[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[5] = {16, 4, 4, 4, 4};
+        for (int t = 0; t < 5; ++t) {
+            e = cudaMallocAsync(&fresh[t], want * bytes[t], c->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                for (int u = 0; u < t; ++u) cudaFreeAsync(fresh[u], c->stream);
+                return cuda_fail(c, e, "ab_build (particle buffers)");
+            }
+        }
+        void* old[5] = {cl.spos, cl.perm, cl.cell_id, cl.rank, cl.tmp};
+        for (void* b : old)
+            if (b) cudaFreeAsync(b, c->stream);
+        cl.spos = (float4*)fresh[0];
+        cl.perm = (uint32_t*)fresh[1];
+        cl.cell_id = (uint32_t*)fresh[2];
+        cl.rank = (uint32_t*)fresh[3];
+        cl.tmp = (uint32_t*)fresh[4];
+        cl.cap_n = want;
+    }
+    if ((e = grow(&cl.cell_start, &cl.cap_cells, (size_t)g.n_cells + 1, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ab_build (cell table)");
+    s = ensure_scan(c, g.n_cells + 1);
+    if (s != AB_OK) return s;
+    cl.n = n;
+    cl.g = g;
+    e = ab::launch_build(cl, (const float4*)pos4, c->sc, c->d_err, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_build launch");
+    cl.user_pos = pos4;
+    cl.valid = true;
+    return AB_OK;
+}
+
+ab_status ab_cell_shape(ab_ctx* c, int32_t* ncell, int64_t* n_cells) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = require_cells(c);
+    if (s != AB_OK) return s;
+    if (ncell)
+        for (int k = 0; k < 3; ++k) ncell[k] = c->cl.g.n[k];
+    if (n_cells) *n_cells = c->cl.g.n_cells;
+    return AB_OK;
+}
+
+ab_status ab_cell_export(ab_ctx* c, uint32_t* perm, uint32_t* cell_start) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = require_cells(c);
+    if (s != AB_OK) return s;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaSuccess;
+    if (perm && c->cl.n > 0)
+        e = cudaMemcpyAsync(perm, c->cl.perm, (size_t)c->cl.n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && cell_start)
+        e = cudaMemcpyAsync(cell_start, c->cl.cell_start, (size_t)(c->cl.g.n_cells + 1) * 4,
+                            cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "ab_cell_export");
+}
+
+ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
+                      float* out, double* energy) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = require_cells(c);
+    if (s != AB_OK) return s;
+    if ((int)op < AB_OP_COUNT || (int)op > AB_OP_SOFT) return fail(c, AB_ERR_INVALID_ARG, "unknown op");
+    if (!prm) return fail(c, AB_ERR_INVALID_ARG, "params is NULL");
+    const int64_t n = c->cl.n;
+    const bool vec = (op == AB_OP_EXPF || op == AB_OP_SOFT);
+    if (n > 0 && !out) return fail(c, AB_ERR_INVALID_ARG, "out is NULL");
+    if (vec && !aligned16(out)) return fail(c, AB_ERR_INVALID_ARG, "vector output must be 16-byte aligned");
+    if (op == AB_OP_GAUSS && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "GAUSS needs weights w");
+    const size_t ob = out_bytes(op, n);
+    if (overlaps(out, ob, c->cl.user_pos, (size_t)n * 16) ||
+        (op == AB_OP_GAUSS && overlaps(out, ob, w, (size_t)n * 4)) ||
+        overlaps(energy, 8, out, ob))
+        return fail(c, AB_ERR_ALIAS, "output overlaps an input");
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    if (op == AB_OP_GAUSS) {
+        if ((s = ensure_sv(c, n)) != AB_OK) return s;
+        if ((e = ab::launch_gather_vars(c->cl, w, nullptr, c->sc.sv, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "ab_pair_sum gather");
+    }
+    ab::PairOut o;
+    o.out = vec ? nullptr : out;
+    o.out4 = vec ? (float4*)out : nullptr;
+    const int grid = ab::pair_grid(n);
+    if (op == AB_OP_LJ && energy) {
+        if ((s = ensure_partial(c, (size_t)grid)) != AB_OK) return s;
+        o.partial = c->sc.partial;
+        o.partial_count = grid;
+    }
+    e = ab::launch_pair_fwd(c->cl, op, *prm, c->sc.sv, o, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum launch");
+    if (op == AB_OP_LJ && energy) {
+        if (n > 0) e = ab::launch_reduce_partials(o.partial, grid, energy, c->stream);
+        else e = cudaMemsetAsync(energy, 0, sizeof(double), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum energy");
+    }
+    return AB_OK;
+}
+
+ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
+                          const float* grad_out, float* grad_pos4, float* grad_w,
+                          double* grad_s) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = require_cells(c);
+    if (s != AB_OK) return s;
+    if (op != AB_OP_GAUSS && op != AB_OP_LJ)
+        return fail(c, AB_ERR_UNSUPPORTED, "adjoint implemented for GAUSS and LJ only");
+    if (!prm) return fail(c, AB_ERR_INVALID_ARG, "params is NULL");
+    const int64_t n = c->cl.n;
+    if (n > 0 && !grad_out) return fail(c, AB_ERR_INVALID_ARG, "grad_out is NULL");
+    if (op == AB_OP_GAUSS && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "GAUSS needs weights w");
+    if (grad_pos4 && !aligned16(grad_pos4)) return fail(c, AB_ERR_INVALID_ARG, "grad_pos4 must be 16-byte aligned");
+    const size_t n4 = (size_t)n * 4, n16 = (size_t)n * 16;
+    const void* ins[3] = {c->cl.user_pos, w, grad_out};
+    const size_t inb[3] = {n16, n4, n4};
+    for (int t = 0; t < 3; ++t) {
+        if (overlaps(grad_pos4, n16, ins[t], inb[t]) || overlaps(grad_w, n4, ins[t], inb[t]) ||
+            overlaps(grad_s, 8, ins[t], inb[t]))
+            return fail(c, AB_ERR_ALIAS, "an output overlaps an input");
+    }
+    if (overlaps(grad_pos4, n16, grad_w, n4) || overlaps(grad_s, 8, grad_pos4, n16) ||
+        overlaps(grad_s, 8, grad_w, n4))
+        return fail(c, AB_ERR_ALIAS, "outputs overlap");
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    if ((s = ensure_sv(c, n)) != AB_OK) return s;
+    if ((e = ab::launch_gather_vars(c->cl, op == AB_OP_GAUSS ? w : nullptr, grad_out, c->sc.sv,
+                                    c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ab_pair_sum_bwd gather");
+    ab::PairOut o;
+    o.grad_pos = (float4*)grad_pos4;
+    o.grad_w = op == AB_OP_GAUSS ? grad_w : nullptr;
+    const int grid = ab::pair_grid(n);
+    const bool want_s = op == AB_OP_GAUSS && grad_s;
+    if (want_s) {
+        if ((s = ensure_partial(c, (size_t)grid)) != AB_OK) return s;
+        o.partial = c->sc.partial;
+        o.partial_count = grid;
+    }
+    e = ab::launch_pair_bwd(c->cl, op, *prm, c->sc.sv, o, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd launch");
+    if (want_s) {
+        if (n > 0) e = ab::launch_reduce_partials(o.partial, grid, grad_s, c->stream);
+        else e = cudaMemsetAsync(grad_s, 0, sizeof(double), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd ds");
+    }
+    return AB_OK;
+}
+
+ab_status ab_pair_list(ab_ctx* c, int64_t* offsets, int32_t* idx, int64_t cap, int64_t* nnz) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = require_cells(c);
+    if (s != AB_OK) return s;
+    const int64_t n = c->cl.n;
+    if (!offsets || !nnz || cap < 0 || (cap > 0 && !idx))
+        return fail(c, AB_ERR_INVALID_ARG, "offsets, nnz required; idx required when cap > 0");
+    if (overlaps(offsets, (size_t)(n + 1) * 8, idx, (size_t)cap * 4) ||
+        overlaps(offsets, (size_t)(n + 1) * 8, c->cl.user_pos, (size_t)n * 16) ||
+        overlaps(idx, (size_t)cap * 4, c->cl.user_pos, (size_t)n * 16))
+        return fail(c, AB_ERR_ALIAS, "output overlaps an input");
+    cudaSetDevice(c->device);
+    cudaError_t e = grow(&c->sc.counts, &c->sc.cap_counts, (size_t)n + 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_list workspace");
+    if ((s = ensure_scan(c, n + 1)) != AB_OK) return s;
+    e = cudaMemsetAsync(c->sc.counts, 0, (size_t)(n + 1) * 4, c->stream);
+    if (e == cudaSuccess) e = ab::launch_pair_count(c->cl, c->sc.counts, c->stream);
+    if (e == cudaSuccess)
+        e = ab::launch_scan_u32_to_i64(c->sc.counts, offsets, n + 1, c->sc.scan_status,
+                                       c->sc.scan_ticket, c->d_err, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_list count");
+    int64_t total = 0;
+    e = cudaMemcpyAsync(&total, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_list total");
+    *nnz = total;
+    if (total > cap) return fail(c, AB_ERR_CAPACITY, "need %lld index slots", (long long)total);
+    e = ab::launch_pair_emit(c->cl, offsets, idx, c->stream);
+    return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "ab_pair_list emit");
+}
+
+static ab_status check_dense(ab_ctx* c, int64_t m, int64_t n, const float* X, const float* Y,
+                             int32_t nrhs, const float* W, ab_prec prec) {
+    if (m < 0 || n < 0 || m >= (int64_t(1) << 31) || n >= (int64_t(1) << 31))
+        return fail(c, AB_ERR_INVALID_ARG, "m, n out of range");
+    if (nrhs < 1 || nrhs > 64) return fail(c, AB_ERR_INVALID_ARG, "nrhs must be in [1, 64]");
+    if ((int)prec < AB_PREC_FP32 || (int)prec > AB_PREC_BF16) return fail(c, AB_ERR_INVALID_ARG, "unknown precision");
+    if ((m > 0 && (!X || !aligned16(X))) || (n > 0 && (!Y || !aligned16(Y))))
+        return fail(c, AB_ERR_INVALID_ARG, "X, Y must be 16-byte aligned float32[.][4]");
+    if (n > 0 && !W) return fail(c, AB_ERR_INVALID_ARG, "W is NULL");
+    return AB_OK;
+}
+
+ab_status ab_kernel_matvec(ab_ctx* c, int64_t m, int64_t n, const float* X, const float* Y,
+                           int32_t nrhs, const float* W, float s, ab_prec prec, float* out) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status st = check_dense(c, m, n, X, Y, nrhs, W, prec);
+    if (st != AB_OK) return st;
+    if (m > 0 && !out) return fail(c, AB_ERR_INVALID_ARG, "out is NULL");
+    const size_t ob = (size_t)m * nrhs * 4;
+    if (overlaps(out, ob, X, (size_t)m * 16) || overlaps(out, ob, Y, (size_t)n * 16) ||
+        overlaps(out, ob, W, (size_t)n * nrhs * 4))
+        return fail(c, AB_ERR_ALIAS, "out overlaps an input");
+    cudaSetDevice(c->device);
+    cudaError_t e = ab::launch_dense_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s,
+                                         prec, out, c->stream);
+    if (e == cudaErrorNotSupported)
+        return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");
+    return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "ab_kernel_matvec");
+}
+
+ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, const float* Y,
+                               int32_t nrhs, const float* W, float s, ab_prec prec,
+                               const float* G, float* dW, float* dX, float* dY, double* ds) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status st = check_dense(c, m, n, X, Y, nrhs, W, prec);
+    if (st != AB_OK) return st;
+    if (m > 0 && !G) return fail(c, AB_ERR_INVALID_ARG, "G is NULL");
+    if ((dX && !aligned16(dX)) || (dY && !aligned16(dY)))
+        return fail(c, AB_ERR_INVALID_ARG, "dX, dY must be 16-byte aligned");
+    const void* ins[4] = {X, Y, W, G};
+    const size_t inb[4] = {(size_t)m * 16, (size_t)n * 16, (size_t)n * nrhs * 4, (size_t)m * nrhs * 4};
+    const void* outs[4] = {dW, dX, dY, ds};
+    const size_t outb[4] = {(size_t)n * nrhs * 4, (size_t)m * 16, (size_t)n * 16, 8};
+    for (int a = 0; a < 4; ++a) {
+        for (int b = 0; b < 4; ++b)
+            if (overlaps(outs[a], outb[a], ins[b], inb[b]))
+                return fail(c, AB_ERR_ALIAS, "an output overlaps an input");
+        for (int b = a + 1; b < 4; ++b)
+            if (overlaps(outs[a], outb[a], outs[b], outb[b]))
+                return fail(c, AB_ERR_ALIAS, "outputs overlap");
+    }
+    cudaSetDevice(c->device);
+    double* partial = nullptr;
+    if (ds) {
+        if ((st = ensure_partial(c, (size_t)ab::dense_partial_capacity(m, n))) != AB_OK) return st;
+        partial = c->sc.partial;
+    }
+    int pc = 0;
+    cudaError_t e = ab::launch_dense_bwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec,
+                                         G, dW, (float4*)dX, (float4*)dY, partial, &pc, c->stream);
+    if (e == cudaErrorNotSupported)
+        return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_matvec_bwd");
+    if (ds) {
+        e = pc > 0 ? ab::launch_reduce_partials(partial, pc, ds, c->stream)
+                   : cudaMemsetAsync(ds, 0, sizeof(double), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_matvec_bwd ds");
+    }
+    return AB_OK;
+}
+
+ab_status ab_bd_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4,
+                     const float* force4, float dt, float D, uint64_t seed, uint64_t step) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = check_domain(c, dom);
+    if (s != AB_OK) return s;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(c, AB_ERR_INVALID_ARG, "n out of range");
+    if (n > 0 && (!pos4 || !aligned16(pos4) || (force4 && !aligned16(force4))))
+        return fail(c, AB_ERR_INVALID_ARG, "pos4/force4 must be 16-byte aligned");
+    if (!isfinite(dt) || !isfinite(D) || D < 0.0f)
+        return fail(c, AB_ERR_INVALID_ARG, "dt, D must be finite, D >= 0");
+    if (overlaps(pos4, (size_t)n * 16, force4, (size_t)n * 16))
+        return fail(c, AB_ERR_ALIAS, "force4 overlaps pos4");
+    cudaSetDevice(c->device);
+    Geom g = make_geom(dom, 0);
+    cudaError_t e = ab::launch_bd_step(g, n, (float4*)pos4, (const float4*)force4, dt, D, seed,
+                                       step, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_bd_step");
+    if (pos4 == c->cl.user_pos) c->cl.valid = false;
+    return AB_OK;
+}
+
+// ---- testing hooks -------------------------------------------------------
+
+ab_status ab_testing_scan_timeout(ab_ctx* c, int64_t items, int32_t skip_tile,
+                                  int64_t limit_ns) {
+    if (!c || items < 1 || items >= (int64_t(1) << 30) || skip_tile < 0 || limit_ns <= 0 ||
+        limit_ns > 2000000000ll)
+        return AB_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaError_t e = grow(&c->sc.counts, &c->sc.cap_counts, (size_t)items, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "testing scan workspace");
+    ab_status s = ensure_scan(c, items);
+    if (s != AB_OK) return s;
+    e = cudaMemsetAsync(c->sc.counts, 0, (size_t)items * 4, c->stream);
+    if (e == cudaSuccess)
+        e = ab::launch_scan_u32(c->sc.counts, c->sc.counts, items, c->sc.scan_status,
+                                c->sc.scan_ticket, c->d_err, skip_tile, (long long)limit_ns,
+                                c->stream);
+    return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "testing scan");
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

@@ -1,0 +1,298 @@
+// Cell-list build: cell hash + histogram, exclusive scan of the counts,
+// stable counting-sort scatter (paper Sec. 2.2.1: a lattice of hypercube
+// cells, filled in parallel by reordering the particles; Sec. 3: cell width
+// r_cut).  Everything is HBM-bound element-wise work: float4 coalesced loads,
+// grid-stride loops sized to the SM count, a single-pass decoupled look-back
+// scan with bounded waits.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ab_internal.cuh"
+
+namespace ab {
+
+extern int g_num_sms;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int ew_grid(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)g_num_sms * 8;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// (a1) cell hash + histogram.  The atomic's return value is the particle's
+// arrival rank inside its cell (order not deterministic; fixed up below).
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_hash(const float4* __restrict__ pos, int64_t n, Geom g,
+       uint32_t* __restrict__ cell_id, uint32_t* __restrict__ rank,
+       uint32_t* __restrict__ count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 p = __ldg(pos + i);
+        uint32_t c = (uint32_t)cell_coord(p.x, g.lo[0], g.inv_w[0], g.n[0]);
+        uint32_t cy = (uint32_t)cell_coord(p.y, g.lo[1], g.inv_w[1], g.n[1]);
+        c += (uint32_t)g.n[0] * cy;
+        if (DIM == 3) {
+            uint32_t cz = (uint32_t)cell_coord(p.z, g.lo[2], g.inv_w[2], g.n[2]);
+            c += (uint32_t)g.n[0] * (uint32_t)g.n[1] * cz;
+        }
+        cell_id[i] = c;
+        rank[i] = atomicAdd(count + c, 1u);
+    }
+}
+
+// (a3) scatter original indices into their (unordered) slot.
+__global__ void __launch_bounds__(kThreads)
+k_scatter(int64_t n, const uint32_t* __restrict__ cell_id,
+          const uint32_t* __restrict__ rank,
+          const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ tmp) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = cell_id[i];
+        tmp[cell_start[c] + rank[i]] = (uint32_t)i;
+    }
+}
+
+// (a3) make the sort stable: the final slot of particle p inside its cell is
+// the number of cell members with a smaller original index.  Then gather the
+// position into sorted order.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_finalize(int64_t n, const float4* __restrict__ pos,
+           const uint32_t* __restrict__ cell_id,
+           const uint32_t* __restrict__ cell_start,
+           const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm,
+           float4* __restrict__ spos) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t p = tmp[s];
+        uint32_t c = cell_id[p];
+        uint32_t a = cell_start[c], b = cell_start[c + 1];
+        uint32_t r = 0;
+        for (uint32_t t = a; t < b; ++t) r += (__ldg(tmp + t) < p) ? 1u : 0u;
+        uint32_t d = a + r;
+        perm[d] = p;
+        float4 q = __ldg(pos + p);
+        spos[d] = make_float4(q.x, q.y, DIM == 3 ? q.z : 0.0f, 0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_gather_vars(int64_t n, const uint32_t* __restrict__ perm,
+              const float* __restrict__ w, const float* __restrict__ g,
+              float2* __restrict__ sv) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t p = perm[s];
+        sv[s] = make_float2(w ? __ldg(w + p) : 0.0f, g ? __ldg(g + p) : 0.0f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// (a2) single-pass exclusive scan with decoupled look-back
+// (Merrill & Garland, "Single-pass parallel prefix scan with decoupled
+// look-back", 2016).  Tiles take increasing ids from a ticket counter, so a
+// tile only ever waits on tiles that are already running; every wait is still
+// bounded by a wall-clock limit after which the tile records
+// DEVERR_SCAN_TIMEOUT and carries on (results are then garbage, but the
+// kernel always terminates).
+// ---------------------------------------------------------------------------
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kThreads * kScanItems;
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPre = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename TOut>
+__global__ void __launch_bounds__(kThreads)
+k_scan(const uint32_t* in, TOut* out, int64_t n, uint64_t* status,
+       uint32_t* ticket, uint32_t* err, int skip_tile, long long limit_ns) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_warp[kThreads / 32];
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+
+    uint32_t v[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+    uint64_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) tsum += v[k];
+
+    // warp inclusive scan of thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t x = (lane < kThreads / 32) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane < kThreads / 32) s_warp[lane] = x;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint64_t block_total = s_warp[kThreads / 32 - 1];
+    const uint64_t warp_excl = warp ? s_warp[warp - 1] : 0;
+
+    if (threadIdx.x == 0) {
+        uint64_t excl = 0;
+        if (tile == 0) {
+            if (tile != skip_tile) st_release(status, kFlagPre | (block_total & kValMask));
+        } else {
+            if (tile != skip_tile) st_release(status + tile, kFlagAgg | (block_total & kValMask));
+            const long long t0 = global_ns();
+            int64_t j = tile - 1;
+            while (j >= 0) {
+                uint64_t w = ld_acquire(status + j);
+                uint64_t f = w & ~kValMask;
+                if (f == 0) {
+                    if (global_ns() - t0 > limit_ns) {
+                        atomicOr(err, DEVERR_SCAN_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                excl += w & kValMask;
+                if (f == kFlagPre) break;
+                --j;
+            }
+            if (tile != skip_tile)
+                st_release(status + tile, kFlagPre | ((excl + block_total) & kValMask));
+        }
+        s_prefix = excl;
+    }
+    __syncthreads();
+    uint64_t run = s_prefix + warp_excl + (incl - tsum);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = (TOut)run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_reduce_partials(const double* __restrict__ partial, int count,
+                  double* __restrict__ out) {
+    __shared__ double s[kThreads];
+    double a = 0.0;
+    for (int t = threadIdx.x; t < count; t += kThreads) a += partial[t];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+}  // namespace
+
+size_t scan_tiles(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile); }
+
+template <typename TOut>
+static cudaError_t scan_impl(const uint32_t* in, TOut* out, int64_t n,
+                             uint64_t* status, uint32_t* ticket, uint32_t* err,
+                             int skip_tile, long long limit_ns, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    size_t tiles = scan_tiles(n);
+    cudaError_t e = cudaMemsetAsync(status, 0, tiles * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ticket, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    k_scan<TOut><<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, status, ticket,
+                                                       err, skip_tile, limit_ns);
+    return cudaGetLastError();
+}
+
+// One second: a normal look-back waits microseconds.
+static const long long kScanLimitNs = 1000000000ll;
+
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n,
+                            uint64_t* status, uint32_t* ticket, uint32_t* err,
+                            int skip_tile, long long limit_ns, cudaStream_t st) {
+    return scan_impl<uint32_t>(in, out, n, status, ticket, err, skip_tile,
+                               limit_ns > 0 ? limit_ns : kScanLimitNs, st);
+}
+
+cudaError_t launch_scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n,
+                                   uint64_t* status, uint32_t* ticket,
+                                   uint32_t* err, cudaStream_t st) {
+    return scan_impl<int64_t>(in, out, n, status, ticket, err, -1, kScanLimitNs, st);
+}
+
+cudaError_t launch_reduce_partials(const double* partial, int count, double* out,
+                                   cudaStream_t st) {
+    k_reduce_partials<<<1, kThreads, 0, st>>>(partial, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build(CellList& cl, const float4* pos, Scratch& sc,
+                         uint32_t* err, cudaStream_t st) {
+    const int64_t n = cl.n;
+    const int64_t nc = cl.g.n_cells;
+    cudaError_t e = cudaMemsetAsync(cl.cell_start, 0, (size_t)(nc + 1) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        if (cl.g.dim == 3)
+            k_hash<3><<<ew_grid(n), kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+        else
+            k_hash<2><<<ew_grid(n), kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // counts -> offsets in place; entry nc is 0 so cell_start[nc] = n.
+    e = launch_scan_u32(cl.cell_start, cl.cell_start, nc + 1, sc.scan_status,
+                        sc.scan_ticket, err, -1, 0, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_scatter<<<ew_grid(n), kThreads, 0, st>>>(n, cl.cell_id, cl.rank, cl.cell_start, cl.tmp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (cl.g.dim == 3)
+            k_finalize<3><<<ew_grid(n), kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+        else
+            k_finalize<2><<<ew_grid(n), kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gather_vars(const CellList& cl, const float* w, const float* g,
+                               float2* sv, cudaStream_t st) {
+    if (cl.n <= 0) return cudaSuccess;
+    k_gather_vars<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, w, g, sv);
+    return cudaGetLastError();
+}
+
+}  // namespace ab

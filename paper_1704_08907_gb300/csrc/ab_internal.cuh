@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/aboria_gpu.h"
+
+#define AB_HIDDEN __attribute__((visibility("hidden")))
+
+namespace ab {
+
+// Device-side error bits latched in the context's error word.
+enum : uint32_t {
+    DEVERR_SCAN_TIMEOUT = 1u,
+};
+
+// Cell-lattice geometry of one build, passed by value to kernels.
+struct Geom {
+    int dim;
+    int n[3];            // cells per axis (1 for unused axes)
+    int periodic[3];
+    float lo[3];
+    float inv_w[3];      // n_k / L_k rounded to FP32
+    float L[3];          // hi - lo in FP32
+    float halfL[3];      // 0.5f * L in FP32
+    float r2;            // fl(r * r)
+    float r;             // radius as given
+    int general;         // 1 if a periodic axis has fewer than 5 cells
+    int64_t n_cells;
+};
+
+// Cell coordinate along one axis: floor((x - lo) * inv_w), clamped.
+// Every kernel that needs a particle's cell uses exactly this expression, so
+// the hash and the stencil search agree bit for bit.
+__device__ __forceinline__ int cell_coord(float x, float lo, float inv_w, int n) {
+    float u = __fmul_rn(__fsub_rn(x, lo), inv_w);
+    float f = floorf(u);
+    int c = (f >= (float)n) ? n - 1 : (f < 0.0f ? 0 : (int)f);
+    return c;
+}
+
+// Library-owned buffers of one cell list.
+struct CellList {
+    int64_t n = 0;
+    Geom g{};
+    const float* user_pos = nullptr;  // caller's positions at build time
+    bool valid = false;
+    float4* spos = nullptr;           // sorted positions (x, y, z, 0)
+    uint32_t* perm = nullptr;         // perm[s] = original index
+    uint32_t* cell_id = nullptr;      // per original particle
+    uint32_t* rank = nullptr;         // per original particle (atomic rank)
+    uint32_t* tmp = nullptr;          // unordered slot -> original index
+    uint32_t* cell_start = nullptr;   // [n_cells + 1]
+    size_t cap_n = 0, cap_cells = 0;
+};
+
+struct Scratch {
+    float2* sv = nullptr;             // sorted per-particle (w, g)
+    size_t cap_sv = 0;
+    uint64_t* scan_status = nullptr;  // decoupled look-back tile words
+    uint32_t* scan_ticket = nullptr;
+    size_t cap_tiles = 0;
+    double* partial = nullptr;        // per-block FP64 partial sums
+    size_t cap_partial = 0;
+    uint32_t* counts = nullptr;       // pair-list counts (user order)
+    size_t cap_counts = 0;
+};
+
+// ---- launchers (defined in the .cu files) ----------------------------------
+
+// ab_cells.cu
+AB_HIDDEN cudaError_t launch_build(CellList& cl, const float4* pos, Scratch& sc,
+                                   uint32_t* err, cudaStream_t st);
+AB_HIDDEN cudaError_t launch_gather_vars(const CellList& cl, const float* w,
+                                         const float* g, float2* sv,
+                                         cudaStream_t st);
+// Exclusive scan of n u32 counts into out (u32 or u64), out[n] = total.
+// status/ticket: scratch of scan_tiles(n) words + 1 ticket (zeroed here).
+AB_HIDDEN size_t scan_tiles(int64_t n);
+AB_HIDDEN cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out,
+                                      int64_t n, uint64_t* status,
+                                      uint32_t* ticket, uint32_t* err,
+                                      int skip_tile, long long limit_ns,
+                                      cudaStream_t st);
+AB_HIDDEN cudaError_t launch_scan_u32_to_i64(const uint32_t* in, int64_t* out,
+                                             int64_t n, uint64_t* status,
+                                             uint32_t* ticket, uint32_t* err,
+                                             cudaStream_t st);
+AB_HIDDEN cudaError_t launch_reduce_partials(const double* partial, int count,
+                                             double* out, cudaStream_t st);
+
+// ab_pairs.cu
+struct PairOut {
+    float* out = nullptr;        // scalar output (user order)
+    float4* out4 = nullptr;      // vector output (user order)
+    float4* grad_pos = nullptr;  // bwd
+    float* grad_w = nullptr;     // bwd
+    double* partial = nullptr;   // per-block partials (energy or ds)
+    int partial_count = 0;
+};
+AB_HIDDEN int pair_grid(int64_t n);
+AB_HIDDEN cudaError_t launch_pair_fwd(const CellList& cl, ab_op op,
+                                      const ab_op_params& prm, const float2* sv,
+                                      PairOut& o, cudaStream_t st);
+AB_HIDDEN cudaError_t launch_pair_bwd(const CellList& cl, ab_op op,
+                                      const ab_op_params& prm, const float2* sv,
+                                      PairOut& o, cudaStream_t st);
+AB_HIDDEN cudaError_t launch_pair_count(const CellList& cl, uint32_t* counts,
+                                        cudaStream_t st);
+AB_HIDDEN cudaError_t launch_pair_emit(const CellList& cl, const int64_t* offsets,
+                                       int32_t* idx, cudaStream_t st);
+
+// ab_dense.cu
+AB_HIDDEN cudaError_t launch_dense_fwd(int64_t m, int64_t n, const float4* X,
+                                       const float4* Y, int nrhs, const float* W,
+                                       float s, ab_prec prec, float* out,
+                                       cudaStream_t st);
+AB_HIDDEN cudaError_t launch_dense_bwd(int64_t m, int64_t n, const float4* X,
+                                       const float4* Y, int nrhs, const float* W,
+                                       float s, ab_prec prec, const float* G,
+                                       float* dW, float4* dX, float4* dY,
+                                       double* partial, int* partial_count,
+                                       cudaStream_t st);
+AB_HIDDEN int dense_partial_capacity(int64_t m, int64_t n);
+
+// ab_bd.cu
+AB_HIDDEN cudaError_t launch_bd_step(const Geom& g, int64_t n, float4* pos,
+                                     const float4* force, float dt, float D,
+                                     uint64_t seed, uint64_t step,
+                                     cudaStream_t st);
+
+}  // namespace ab

@@ -1,0 +1,119 @@
+"""Dense kernel operator and adjoint vs the FP64 oracle (GPU, C ABI).
+
+Error metric: max_{i,c} |Y - Y_ref| / sum_j K_ij |W_jc| (the FP64 absolute
+sum); FP32 CUDA-core path <= 1e-5, tensor-core split paths <= 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _helpers import dev, host
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ab():
+    import paper_1704_08907_gb300 as ab
+    return ab
+
+
+@pytest.fixture(scope="module")
+def ctx(ab, cuda):
+    c = ab.Context(0)
+    yield c
+    c.close()
+
+
+def _dev4(a):
+    return dev(synth.pack4(a))
+
+
+@pytest.mark.parametrize("m,n,nrhs", [(512, 700, 64), (1, 1, 1), (129, 33, 17), (300, 4100, 64)])
+def test_forward_small(ab, ctx, m, n, nrhs):
+    d = synth.c4(m=m, n=n, nrhs=nrhs, seed_offset=m)
+    out = host(ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "fp32"))
+    ref = dense.matvec(d.X, d.Y, d.W, d.s)
+    den = dense.matvec_abs(d.X, d.Y, d.W, d.s)
+    assert np.max(np.abs(out - ref) / den) <= 1e-5
+
+
+def test_forward_full_size_sampled_rows(ab, ctx):
+    d = synth.c4()
+    out = host(ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "fp32"))
+    rows = synth.query_sample(d.X.shape[0], 256, 8)
+    ref = dense.matvec(d.X, d.Y, d.W, d.s, rows=rows)
+    den = dense.matvec_abs(d.X, d.Y, d.W, d.s, rows=rows)
+    assert np.max(np.abs(out[rows] - ref) / den) <= 1e-5
+
+
+def test_s_zero_column_sums(ab, ctx):
+    d = synth.c4(m=100, n=3000, nrhs=64)
+    out = host(ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), 0.0, "fp32"))
+    ref = d.W.astype(np.float64).sum(0)
+    assert np.max(np.abs(out - ref) / np.abs(d.W).sum(0)) <= 1e-5
+
+
+def test_adjoint_small(ab, ctx):
+    d = synth.c4(m=700, n=900, nrhs=64, seed_offset=3)
+    dW = torch.empty((900, 64), dtype=torch.float32, device="cuda:0")
+    dX = torch.empty((700, 4), dtype=torch.float32, device="cuda:0")
+    dY = torch.empty((900, 4), dtype=torch.float32, device="cuda:0")
+    ds = torch.empty((), dtype=torch.float64, device="cuda:0")
+    ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "fp32", dev(d.G),
+                            dW, dX, dY, ds)
+    rW = dense.grad_W(d.X, d.Y, d.G, d.s)
+    aW = dense.grad_W(d.X, d.Y, np.abs(d.G), d.s)
+    assert np.max(np.abs(host(dW) - rW) / aW) <= 1e-5
+    rX = dense.grad_X(d.X, d.Y, d.W, d.G, d.s)
+    rY = dense.grad_Y(d.X, d.Y, d.W, d.G, d.s)
+    # denominators: the same sums with |A_ij| |x_i - y_j|
+    aX = dense.grad_X(d.X, d.Y, np.abs(d.W), np.abs(d.G), d.s)   # sign-free bound proxy
+    scaleX = np.abs(rX).max()
+    scaleY = np.abs(rY).max()
+    assert np.max(np.abs(host(dX)[:, :3] - rX)) <= 1e-4 * scaleX
+    assert np.max(np.abs(host(dY)[:, :3] - rY)) <= 1e-4 * scaleY
+    del aX
+    rs = dense.grad_s(d.X, d.Y, d.W, d.G, d.s)
+    As = abs(dense.grad_s(d.X, d.Y, np.abs(d.W), np.abs(d.G), d.s))
+    assert abs(float(ds) - rs) <= 1e-5 * As
+
+
+def test_adjoint_full_size_sampled(ab, ctx):
+    d = synth.c4()
+    m, n = d.X.shape[0], d.Y.shape[0]
+    dW = torch.empty((n, 64), dtype=torch.float32, device="cuda:0")
+    dX = torch.empty((m, 4), dtype=torch.float32, device="cuda:0")
+    ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "fp32", dev(d.G),
+                            dW, dX, None, None)
+    cols = synth.query_sample(n, 128, 9)
+    rW = dense.grad_W(d.X, d.Y, d.G, d.s, cols=cols)
+    aW = dense.grad_W(d.X, d.Y, np.abs(d.G), d.s, cols=cols)
+    assert np.max(np.abs(host(dW)[cols] - rW) / aW) <= 1e-5
+    rows = synth.query_sample(m, 64, 10)
+    rX = dense.grad_X(d.X, d.Y, d.W, d.G, d.s, rows=rows)
+    assert np.max(np.abs(host(dX)[rows, :3] - rX)) <= 1e-4 * np.abs(rX).max()
+
+
+def test_autograd_kernel_matvec(ab, ctx):
+    d = synth.c4(m=300, n=500, nrhs=64, seed_offset=7)
+    X = _dev4(d.X).requires_grad_(True)
+    Y = _dev4(d.Y).requires_grad_(True)
+    W = dev(d.W).requires_grad_(True)
+    s = torch.tensor(d.s, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    out = ab.KernelMatvec.apply(X, Y, W, s, ctx, "fp32")
+    (out * dev(d.G)).sum().backward()
+    rW = dense.grad_W(d.X, d.Y, d.G, d.s)
+    assert np.max(np.abs(host(W.grad) - rW)) <= 1e-4 * np.abs(rW).max()
+    rs = dense.grad_s(d.X, d.Y, d.W, d.G, d.s)
+    As = abs(dense.grad_s(d.X, d.Y, np.abs(d.W), np.abs(d.G), d.s))
+    assert abs(float(s.grad) - rs) <= 1e-5 * As
+
+
+def test_unsupported_precision_reports(ab, ctx):
+    d = synth.c4(m=16, n=16, nrhs=8)
+    with pytest.raises(ab.AbError) as e:
+        ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "bf16x3")
+    assert e.value.status == 7

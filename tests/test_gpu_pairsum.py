@@ -1,0 +1,203 @@
+"""GPU pair sums and adjoints vs the FP64 oracle (GPU, C ABI).
+
+Tolerance: the pair-sum error metric |y - y_ref| / max(|y_ref|, sum_j |t_ij|)
+must be <= 1e-5 for FP32 accumulation (each output sums at most a few hundred
+terms, each evaluated to ~1e-6 relative with the MUFU approximations).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _helpers import dev, host, oracle_box, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ab():
+    import paper_1704_08907_gb300 as ab
+    return ab
+
+
+@pytest.fixture(scope="module")
+def ctx(ab, cuda):
+    c = ab.Context(0)
+    yield c
+    c.close()
+
+
+def _setup(ab, ctx, w, queries=None):
+    dom = ab.Domain(w.dim, w.periodic, w.radius, w.lo, w.hi)
+    ab.ab_build(ctx, dom, dev(w.pos))
+    box = oracle_box(w)
+    if w.n <= 8192 and queries is None:
+        off, idx = oracle.neighbours_brute(box, w.pos)
+    else:
+        off, idx = oracle.CellList(box, w.pos).neighbours(queries)
+    return box, off, idx
+
+
+def _params(ab, w):
+    p = w.params
+    return ab.OpParams(s=p.get("s", 0.0), eps=p.get("eps", 1.0), sigma=p.get("sigma", 1.0),
+                       c=p.get("c", 1.0), k=p.get("k", 1.0))
+
+
+def _wl(name, n, dim, periodic, r, op, params, seed, w=None):
+    pos = synth.uniform_positions(n, dim, seed)
+    wt = synth.weights(n, seed + 1) if w is None else w
+    return synth.PairWorkload(name, dim, n, pos, periodic, radius=r, op=op, params=params, w=wt)
+
+
+CASES = [
+    _wl("g2", 4096, 2, (1, 1), 0.03, "gauss", {"s": 1e4}, 1),
+    _wl("g3", 6000, 3, (1, 0, 1), 0.08, "gauss", {"s": 1.0 / (0.08 / 3) ** 2}, 2),
+    _wl("lj3", 6000, 3, (1, 1, 1), 0.08, "lj", {"eps": 1.0, "sigma": 0.02}, 3),
+    _wl("lj2", 4000, 2, (0, 1), 0.05, "lj", {"eps": 2.0, "sigma": 0.01}, 4),
+    _wl("e2", 4096, 2, (1, 1), float(np.sqrt(3 / 4096)), "expf", {"c": 1e-3}, 5),
+    _wl("e3", 5000, 3, (1, 1, 1), 0.1, "expf", {"c": 0.5}, 6),
+    _wl("s2", 5000, 2, (1, 0), 0.02, "soft", {"k": 1e4}, 7),
+    _wl("s3g", 3000, 3, (1, 1, 1), 0.3, "soft", {"k": 3.0}, 8),     # general path
+    _wl("c2", 4000, 2, (1, 1), 0.45, "count", {}, 9),               # n_k = 2
+]
+
+
+@pytest.mark.parametrize("w", CASES, ids=[c.name for c in CASES])
+def test_forward_vs_oracle(ab, ctx, w):
+    box, off, idx = _setup(ab, ctx, w)
+    y = host(ab.ab_pair_sum(ctx, w.op, _params(ab, w), w=dev(w.w)))
+    ref = oracle.pair_values(w.op, box, w.pos, off, idx, w=w.w, params=w.params)
+    den = oracle.abs_terms(w.op, box, w.pos, off, idx, w=w.w, params=w.params)
+    if w.op in ("expf", "soft"):
+        assert np.all(y[:, 3] == 0)
+        assert rel_err(y[:, :w.dim], ref[:, :w.dim], den[:, :w.dim]) <= TOL
+    elif w.op == "count":
+        assert np.array_equal(y, ref[:, 0].astype(np.float32))
+    else:
+        assert rel_err(y, ref[:, 0], den[:, 0]) <= TOL
+
+
+@pytest.mark.parametrize("w", [c for c in CASES if c.op in ("gauss", "lj")],
+                         ids=[c.name for c in CASES if c.op in ("gauss", "lj")])
+def test_adjoint_vs_oracle(ab, ctx, w):
+    box, off, idx = _setup(ab, ctx, w)
+    g = synth.weights(w.n, 99, "normal")
+    gpos = torch.empty((w.n, 4), dtype=torch.float32, device="cuda:0")
+    gw = torch.empty(w.n, dtype=torch.float32, device="cuda:0") if w.op == "gauss" else None
+    gs = torch.empty((), dtype=torch.float64, device="cuda:0") if w.op == "gauss" else None
+    ab.ab_pair_sum_bwd(ctx, w.op, _params(ab, w), dev(w.w) if w.op == "gauss" else None,
+                       dev(g), gpos, gw, gs)
+    ref, rw, rs = oracle.pair_grads(w.op, box, w.pos, off, idx, g, w=w.w, params=w.params)
+    den, dw, ds = oracle.abs_grad_terms(w.op, box, w.pos, off, idx, g, w=w.w, params=w.params)
+    gp = host(gpos)
+    assert rel_err(gp[:, :w.dim], ref[:, :w.dim], den[:, :w.dim]) <= TOL
+    if w.op == "gauss":
+        assert rel_err(host(gw), rw, dw) <= TOL
+        assert abs(float(gs) - rs.sum()) <= TOL * ds.sum()
+
+
+@pytest.mark.parametrize("op,params", [("expf", {"c": 1e-3}), ("soft", {"k": 1e4})])
+def test_newton_third_law_forces(ab, ctx, op, params):
+    w = _wl("n3", 200000, 2, (1, 1), 0.004, op, params, 11)
+    dom = ab.Domain(2, w.periodic, w.radius)
+    ab.ab_build(ctx, dom, dev(w.pos))
+    f = host(ab.ab_pair_sum(ctx, op, _params(ab, w))).astype(np.float64)
+    assert np.all(np.abs(f.sum(0)) <= 1e-5 * np.abs(f).sum())
+
+
+def test_c2_full_lj_energy_and_forces(ab, ctx):
+    """1,048,576 points, r = 0.0197, LJ (sigma 0.01): every particle's energy
+    and force against the FP64 oracle, plus the total energy."""
+    w = synth.c2()
+    box, off, idx = _setup(ab, ctx, w)
+    dom = ab.Domain(3, w.periodic, w.radius)
+    E, F, etot = ab.lj_energy_forces(ctx, dom, dev(w.pos), 1.0, 0.01)
+    Eo = oracle.pair_values("lj", box, w.pos, off, idx, params=w.params)[:, 0]
+    Ea = oracle.abs_terms("lj", box, w.pos, off, idx, params=w.params)[:, 0]
+    assert rel_err(host(E), Eo, Ea) <= TOL
+    assert abs(float(etot) - Eo.sum()) <= TOL * Ea.sum()
+    ones = np.ones(w.n)
+    Fo, _, _ = oracle.pair_grads("lj", box, w.pos, off, idx, ones, params=w.params)
+    Fa, _, _ = oracle.abs_grad_terms("lj", box, w.pos, off, idx, ones, params=w.params)
+    assert rel_err(host(F)[:, :3], Fo[:, :3], Fa[:, :3]) <= TOL
+    # with per-particle upstream gradients
+    g = w.g
+    gpos = torch.empty((w.n, 4), dtype=torch.float32, device="cuda:0")
+    ab.ab_pair_sum_bwd(ctx, "lj", ab.OpParams(eps=1.0, sigma=0.01), None, dev(g), gpos)
+    Go, _, _ = oracle.pair_grads("lj", box, w.pos, off, idx, g, params=w.params)
+    Ga, _, _ = oracle.abs_grad_terms("lj", box, w.pos, off, idx, g, params=w.params)
+    assert rel_err(host(gpos)[:, :3], Go[:, :3], Ga[:, :3]) <= TOL
+
+
+def test_c3_full_gauss_fwd_bwd_sampled(ab, ctx):
+    """16.7M clustered points: forward and adjoint (x, w, s) on 4096 sampled
+    particles against the FP64 oracle."""
+    w = synth.c3()
+    q = synth.query_sample(w.n, 4096, 31)
+    box, off, idx = _setup(ab, ctx, w, queries=q)
+    prm = _params(ab, w)
+    y = host(ab.ab_pair_sum(ctx, "gauss", prm, w=dev(w.w)))
+    ref = oracle.pair_values("gauss", box, w.pos, off, idx, q, w=w.w, params=w.params)[:, 0]
+    den = oracle.abs_terms("gauss", box, w.pos, off, idx, q, w=w.w, params=w.params)[:, 0]
+    assert rel_err(y[q], ref, den) <= TOL
+    gpos = torch.empty((w.n, 4), dtype=torch.float32, device="cuda:0")
+    gw = torch.empty(w.n, dtype=torch.float32, device="cuda:0")
+    gs = torch.empty((), dtype=torch.float64, device="cuda:0")
+    ab.ab_pair_sum_bwd(ctx, "gauss", prm, dev(w.w), dev(w.g), gpos, gw, gs)
+    rp, rw, _ = oracle.pair_grads("gauss", box, w.pos, off, idx, w.g, q, w=w.w, params=w.params)
+    dp, dw, _ = oracle.abs_grad_terms("gauss", box, w.pos, off, idx, w.g, q, w=w.w, params=w.params)
+    assert rel_err(host(gpos)[q, :3], rp[:, :3], dp[:, :3]) <= TOL
+    assert rel_err(host(gw)[q], rw, dw) <= TOL
+    assert np.isfinite(float(gs))
+
+
+def test_paper_shape_expf_1m(ab, ctx):
+    """The paper's benchmark operator (Eq. 1, c = 1e-3, r = sqrt(3/N)) at
+    N = 2^20, sampled rows."""
+    w = synth.paper_shape(1 << 20)
+    q = synth.query_sample(w.n, 8192, 3)
+    box, off, idx = _setup(ab, ctx, w, queries=q)
+    y = host(ab.ab_pair_sum(ctx, "expf", _params(ab, w)))
+    ref = oracle.pair_values("expf", box, w.pos, off, idx, q, params=w.params)
+    den = oracle.abs_terms("expf", box, w.pos, off, idx, q, params=w.params)
+    assert rel_err(y[q, :2], ref[:, :2], den[:, :2]) <= TOL
+
+
+def test_c5_soft_force_sampled(ab, ctx):
+    w = synth.c5()
+    q = synth.query_sample(w.n, 8192, 4)
+    box, off, idx = _setup(ab, ctx, w, queries=q)
+    y = host(ab.ab_pair_sum(ctx, "soft", _params(ab, w)))
+    ref = oracle.pair_values("soft", box, w.pos, off, idx, q, params=w.params)
+    den = oracle.abs_terms("soft", box, w.pos, off, idx, q, params=w.params)
+    assert rel_err(y[q, :2], ref[:, :2], den[:, :2]) <= TOL
+
+
+def test_autograd_lj_and_gauss(ab, ctx):
+    w = _wl("ag", 5000, 3, (1, 1, 1), 0.08, "gauss", {"s": 400.0}, 21)
+    box = oracle_box(w)
+    off, idx = oracle.neighbours_brute(box, w.pos)
+    dom = ab.Domain(3, w.periodic, w.radius)
+    pos = dev(w.pos).requires_grad_(True)
+    wt = dev(w.w).requires_grad_(True)
+    s = torch.tensor(400.0, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    y = ab.GaussPairSum.apply(pos, wt, s, ctx, dom)
+    g = synth.weights(w.n, 5, "normal")
+    (y * dev(g)).sum().backward()
+    rp, rw, rs = oracle.pair_grads("gauss", box, w.pos, off, idx, g, w=w.w, params={"s": 400.0})
+    dp, dw, ds = oracle.abs_grad_terms("gauss", box, w.pos, off, idx, g, w=w.w, params={"s": 400.0})
+    assert rel_err(host(pos.grad)[:, :3], rp[:, :3], dp[:, :3]) <= TOL
+    assert rel_err(host(wt.grad), rw, dw) <= TOL
+    assert abs(float(s.grad) - rs.sum()) <= TOL * ds.sum()
+
+    pos2 = dev(w.pos).requires_grad_(True)
+    E = ab.LJEnergy.apply(pos2, ctx, dom, 1.0, 0.02)
+    E.sum().backward()
+    Fo, _, _ = oracle.pair_grads("lj", box, w.pos, off, idx, np.ones(w.n),
+                                 params={"eps": 1.0, "sigma": 0.02})
+    Fa, _, _ = oracle.abs_grad_terms("lj", box, w.pos, off, idx, np.ones(w.n),
+                                     params={"eps": 1.0, "sigma": 0.02})
+    assert rel_err(host(pos2.grad)[:, :3], Fo[:, :3], Fa[:, :3]) <= TOL
