@@ -80,6 +80,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=30.0):
+        # nvidia-smi's start-up (NVML init) can stall GPU work for seconds:
+        # keep it out of the timed region
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+        self.lines.clear()
+
     def stop(self):
         if self.proc is None:
             return None
@@ -179,6 +187,9 @@ def run_ours(args, rank, world):
         if ev is not None:
             ev[3].record()
 
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -186,8 +197,6 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -292,8 +301,8 @@ def oracle_sample(w, nq, seed=17):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--oracle-queries", type=int, default=131072)
     args = ap.parse_args()

@@ -340,8 +340,9 @@ ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float*
     if (vec && !aligned16(out)) return fail(c, AB_ERR_INVALID_ARG, "vector output must be 16-byte aligned");
     if (op == AB_OP_GAUSS && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "GAUSS needs weights w");
     const size_t ob = out_bytes(op, n);
-    if (overlaps(out, ob, c->cl.user_pos, (size_t)n * 16) ||
-        (op == AB_OP_GAUSS && overlaps(out, ob, w, (size_t)n * 4)) ||
+    // the positions were copied at build time; the inputs here are w only
+    if ((op == AB_OP_GAUSS && overlaps(out, ob, w, (size_t)n * 4)) ||
+        (op == AB_OP_GAUSS && overlaps(energy, 8, w, (size_t)n * 4)) ||
         overlaps(energy, 8, out, ob))
         return fail(c, AB_ERR_ALIAS, "output overlaps an input");
     cudaSetDevice(c->device);
@@ -384,9 +385,9 @@ ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const fl
     if (op == AB_OP_GAUSS && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "GAUSS needs weights w");
     if (grad_pos4 && !aligned16(grad_pos4)) return fail(c, AB_ERR_INVALID_ARG, "grad_pos4 must be 16-byte aligned");
     const size_t n4 = (size_t)n * 4, n16 = (size_t)n * 16;
-    const void* ins[3] = {c->cl.user_pos, w, grad_out};
-    const size_t inb[3] = {n16, n4, n4};
-    for (int t = 0; t < 3; ++t) {
+    const void* ins[2] = {w, grad_out};
+    const size_t inb[2] = {n4, n4};
+    for (int t = 0; t < 2; ++t) {
         if (overlaps(grad_pos4, n16, ins[t], inb[t]) || overlaps(grad_w, n4, ins[t], inb[t]) ||
             overlaps(grad_s, 8, ins[t], inb[t]))
             return fail(c, AB_ERR_ALIAS, "an output overlaps an input");
@@ -427,10 +428,8 @@ ab_status ab_pair_list(ab_ctx* c, int64_t* offsets, int32_t* idx, int64_t cap, i
     const int64_t n = c->cl.n;
     if (!offsets || !nnz || cap < 0 || (cap > 0 && !idx))
         return fail(c, AB_ERR_INVALID_ARG, "offsets, nnz required; idx required when cap > 0");
-    if (overlaps(offsets, (size_t)(n + 1) * 8, idx, (size_t)cap * 4) ||
-        overlaps(offsets, (size_t)(n + 1) * 8, c->cl.user_pos, (size_t)n * 16) ||
-        overlaps(idx, (size_t)cap * 4, c->cl.user_pos, (size_t)n * 16))
-        return fail(c, AB_ERR_ALIAS, "output overlaps an input");
+    if (overlaps(offsets, (size_t)(n + 1) * 8, idx, (size_t)cap * 4))
+        return fail(c, AB_ERR_ALIAS, "offsets overlap idx");
     cudaSetDevice(c->device);
     cudaError_t e = grow(&c->sc.counts, &c->sc.cap_counts, (size_t)n + 1, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_list workspace");

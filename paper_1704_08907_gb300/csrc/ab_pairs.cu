@@ -65,137 +65,221 @@ __device__ __forceinline__ float min_image(float d, float L, float halfL) {
     return d;
 }
 
-// Stencil along axis y or z: up to 3 distinct neighbour cell coordinates and
-// the fast-path shift of each.
-__device__ __forceinline__ int axis_stencil(const Geom& g, int k, int c, bool general,
-                                            int (&cell)[3], float (&shift)[3]) {
+// One neighbour coordinate along axis k for offset o in {-1, 0, +1}: returns
+// false if the offset leaves a non-periodic box or repeats a cell already
+// visited (periodic axes with fewer than 3 cells); *shift receives the
+// fast-path shift (-L when reaching through the lower face, +L through the
+// upper face; only meaningful when every periodic axis has >= 5 cells).
+__device__ __forceinline__ bool stencil_coord(const Geom& g, int k, int c, int o, int& t,
+                                              float& shift) {
     const int n = g.n[k];
-    int m = 0;
-    if (!g.periodic[k]) {
-#pragma unroll
-        for (int o = -1; o <= 1; ++o) {
-            int t = c + o;
-            if (t >= 0 && t < n) { cell[m] = t; shift[m] = 0.0f; ++m; }
-        }
-        return m;
+    t = c + o;
+    shift = 0.0f;
+    if (!g.periodic[k]) return t >= 0 && t < n;
+    if (n == 1) return o == 0;
+    if (n == 2) {                 // cells {0, 1}: offsets 0 and +1 cover both
+        if (o == -1) return false;
+        t = (c + o) & 1;
+        return true;
     }
-    if (general) {
-        // distinct cells of {c-1, c, c+1} mod n (n may be 1 or 2)
-        if (n == 1) { cell[0] = 0; shift[0] = 0.0f; return 1; }
-        if (n == 2) { cell[0] = 0; cell[1] = 1; shift[0] = shift[1] = 0.0f; return 2; }
-        cell[0] = (c + n - 1) % n; cell[1] = c; cell[2] = (c + 1) % n;
-        shift[0] = shift[1] = shift[2] = 0.0f;
-        return 3;
-    }
-    cell[0] = c - 1; shift[0] = 0.0f;
-    if (c == 0) { cell[0] = n - 1; shift[0] = -g.L[k]; }
-    cell[1] = c; shift[1] = 0.0f;
-    cell[2] = c + 1; shift[2] = 0.0f;
-    if (c == n - 1) { cell[2] = 0; shift[2] = g.L[k]; }
-    return 3;
+    if (t < 0) { t += n; shift = -g.L[k]; }
+    else if (t >= n) { t -= n; shift = g.L[k]; }
+    return true;
 }
 
-// Row segments along x: inclusive cell ranges [a, b] and their shifts.
-__device__ __forceinline__ int x_segments(const Geom& g, int c, bool general,
-                                          int (&a)[3], int (&b)[3], float (&shift)[3]) {
-    const int n = g.n[0];
-    if (!g.periodic[0]) {
-        a[0] = c > 0 ? c - 1 : 0;
-        b[0] = c < n - 1 ? c + 1 : n - 1;
-        shift[0] = 0.0f;
-        return 1;
-    }
-    if (general) {
-        if (n <= 3) { a[0] = 0; b[0] = n - 1; shift[0] = 0.0f; return 1; }
-        // n == 4 (n >= 5 periodic never selects the general path on its own,
-        // but the general path is also used for n >= 5 when another axis
-        // needs it): the three distinct cells as contiguous pieces
-        if (c == 0) {
-            a[0] = 0; b[0] = 1; a[1] = n - 1; b[1] = n - 1;
-            shift[0] = shift[1] = 0.0f;
-            return 2;
-        }
-        if (c == n - 1) {
-            a[0] = n - 2; b[0] = n - 1; a[1] = 0; b[1] = 0;
-            shift[0] = shift[1] = 0.0f;
-            return 2;
-        }
-        a[0] = c - 1; b[0] = c + 1; shift[0] = 0.0f;
-        return 1;
-    }
-    if (c == 0) {
-        a[0] = 0; b[0] = 1; shift[0] = 0.0f;
-        a[1] = n - 1; b[1] = n - 1; shift[1] = -g.L[0];
-        return 2;
-    }
-    if (c == n - 1) {
-        a[0] = n - 2; b[0] = n - 1; shift[0] = 0.0f;
-        a[1] = 0; b[1] = 0; shift[1] = g.L[0];
-        return 2;
-    }
-    a[0] = c - 1; b[0] = c + 1; shift[0] = 0.0f;
-    return 1;
+// Value separation along one axis, accurate to one rounding: the canonical
+// minimum image of x_j - x_i, where a wrapped difference is corrected by the
+// rounding error of fl(x_j - x_i) (Knuth's TwoSum).  fl(x_j - x_i) has
+// magnitude above L/2 when it wraps, so fl(. -+ L) is exact (Sterbenz) and
+// only the final addition of the error term rounds.  Without the correction
+// a pair straddling a periodic face would carry an absolute error of
+// ulp(L)/2 in a separation of size ~r.  The neighbour predicate never uses
+// this value; it uses the canonical FP32 rule only.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-// Visit every neighbour j of sorted particle s (position pi):
-// f(j, pj, dx, dy, dz, d2) is called for each accepted pair.
-template <int DIM, bool GENERAL, class F>
-__device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
-                                            const float4& pi, F&& f) {
+__device__ __forceinline__ float value_sep(float xi, float xj, bool periodic, float L,
+                                           float halfL) {
+    const float s = __fsub_rn(xj, xi);
+    if (periodic && (s > halfL || s < -halfL)) {
+        const float e = two_sum_err(xj, -xi, s);
+        const float w = (s > halfL) ? __fsub_rn(s, L) : __fadd_rn(s, L);
+        return __fadd_rn(w, e);
+    }
+    return s;
+}
+
+// Walk the stencil of the particle at pi: seg(a, b, sx, sy, sz) is called for
+// each contiguous range [a, b) of sorted particles with its fast-path shift.
+// Rows along x are contiguous in sorted order; a row that wraps through the
+// periodic x face splits into two segments.
+template <int DIM, bool GENERAL, class S>
+__device__ __forceinline__ void for_each_segment(const PairParams& P, const float4& pi,
+                                                 S&& seg) {
     const Geom& g = P.g;
     const int cx = cell_coord(pi.x, g.lo[0], g.inv_w[0], g.n[0]);
     const int cy = cell_coord(pi.y, g.lo[1], g.inv_w[1], g.n[1]);
     const int cz = DIM == 3 ? cell_coord(pi.z, g.lo[2], g.inv_w[2], g.n[2]) : 0;
-    int ycell[3], zcell[3];
-    float yshift[3], zshift[3];
-    const int ny = axis_stencil(g, 1, cy, GENERAL, ycell, yshift);
-    int nz = 1;
-    zcell[0] = 0;
-    zshift[0] = 0.0f;
-    if (DIM == 3) nz = axis_stencil(g, 2, cz, GENERAL, zcell, zshift);
-    int xa[3], xb[3];
-    float xshift[3];
-    const int nseg = x_segments(g, cx, GENERAL, xa, xb, xshift);
-    const float r2 = g.r2;
-
+    const int nx = g.n[0];
+    // x segments: [xa0, xb0] with shift xs0, optional [xa1, xb1] with xs1
+    int xa0, xb0, xa1 = 0, xb1 = -1;
+    float xs0 = 0.0f, xs1 = 0.0f;
+    if (!g.periodic[0]) {
+        xa0 = cx > 0 ? cx - 1 : 0;
+        xb0 = cx < nx - 1 ? cx + 1 : nx - 1;
+    } else if (nx <= 3) {
+        xa0 = 0;
+        xb0 = nx - 1;
+    } else if (cx == 0) {
+        xa0 = 0; xb0 = 1; xa1 = nx - 1; xb1 = nx - 1; xs1 = GENERAL ? 0.0f : -g.L[0];
+    } else if (cx == nx - 1) {
+        xa0 = nx - 2; xb0 = nx - 1; xa1 = 0; xb1 = 0; xs1 = GENERAL ? 0.0f : g.L[0];
+    } else {
+        xa0 = cx - 1; xb0 = cx + 1;
+    }
 #pragma unroll 1
-    for (int iz = 0; iz < nz; ++iz) {
+    for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
+        int z = 0;
+        float sz = 0.0f;
+        if (DIM == 3 && !stencil_coord(g, 2, cz, oz, z, sz)) continue;
 #pragma unroll 1
-        for (int iy = 0; iy < ny; ++iy) {
-            const int64_t row = ((int64_t)zcell[iz] * g.n[1] + ycell[iy]) * g.n[0];
-            const float sy = yshift[iy], sz = zshift[iz];
-#pragma unroll 1
-            for (int sg = 0; sg < nseg; ++sg) {
-                const uint32_t a = __ldg(P.cell_start + row + xa[sg]);
-                const uint32_t b = __ldg(P.cell_start + row + xb[sg] + 1);
-                const float sx = xshift[sg];
-#pragma unroll 2
-                for (uint32_t j = a; j < b; ++j) {
-                    const float4 pj = __ldg(P.spos + j);
-                    float dx = __fsub_rn(pj.x, pi.x);
-                    float dy = __fsub_rn(pj.y, pi.y);
-                    float dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
-                    if (GENERAL) {
-                        if (g.periodic[0]) dx = min_image(dx, g.L[0], g.halfL[0]);
-                        if (g.periodic[1]) dy = min_image(dy, g.L[1], g.halfL[1]);
-                        if (DIM == 3 && g.periodic[2]) dz = min_image(dz, g.L[2], g.halfL[2]);
-                    } else {
-                        dx = __fadd_rn(dx, sx);
-                        dy = __fadd_rn(dy, sy);
-                        if (DIM == 3) dz = __fadd_rn(dz, sz);
-                    }
-                    float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-                    if (DIM == 3) d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
-                    if (d2 < r2 && j != s) f(j, pj, dx, dy, dz, d2);
-                }
-            }
+        for (int oy = -1; oy <= 1; ++oy) {
+            int y;
+            float sy;
+            if (!stencil_coord(g, 1, cy, oy, y, sy)) continue;
+            if (GENERAL) sy = sz = 0.0f;
+            const int64_t row = ((int64_t)z * g.n[1] + y) * nx;
+            seg(__ldg(P.cell_start + row + xa0), __ldg(P.cell_start + row + xb0 + 1), xs0, sy, sz);
+            if (xb1 >= xa1)
+                seg(__ldg(P.cell_start + row + xa1), __ldg(P.cell_start + row + xb1 + 1), xs1, sy, sz);
         }
     }
 }
 
+// Predicate separation (canonical FP32 rule) for candidate pj.
+template <int DIM, bool GENERAL, bool SHIFTED>
+__device__ __forceinline__ float pred_d2(const Geom& g, const float4& pi, const float4& pj,
+                                         float sx, float sy, float sz, float& dx, float& dy,
+                                         float& dz) {
+    dx = __fsub_rn(pj.x, pi.x);
+    dy = __fsub_rn(pj.y, pi.y);
+    dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
+    if (GENERAL) {
+        if (g.periodic[0]) dx = min_image(dx, g.L[0], g.halfL[0]);
+        if (g.periodic[1]) dy = min_image(dy, g.L[1], g.halfL[1]);
+        if (DIM == 3 && g.periodic[2]) dz = min_image(dz, g.L[2], g.halfL[2]);
+    } else if (SHIFTED) {
+        dx = __fadd_rn(dx, sx);
+        dy = __fadd_rn(dy, sy);
+        if (DIM == 3) dz = __fadd_rn(dz, sz);
+    }
+    float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (DIM == 3) d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+    return d2;
+}
+
+// Direct visit: f(j, pj, dx, dy, dz, d2) for every accepted pair, with value
+// separations accurate to one rounding (see value_sep).  Used for operators
+// whose per-pair body is a few instructions.
+template <int DIM, bool GENERAL, class F>
+__device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
+                                            const float4& pi, F&& f) {
+    const Geom& g = P.g;
+    const float r2 = g.r2;
+    for_each_segment<DIM, GENERAL>(P, pi, [&](uint32_t a, uint32_t b, float sx, float sy,
+                                              float sz) {
+        if (GENERAL || sx != 0.0f || sy != 0.0f || sz != 0.0f) {
+#pragma unroll 1
+            for (uint32_t j = a; j < b; ++j) {
+                const float4 pj = __ldg(P.spos + j);
+                float dx, dy, dz;
+                const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz);
+                if (d2 < r2 && j != s) {
+                    dx = value_sep(pi.x, pj.x, g.periodic[0], g.L[0], g.halfL[0]);
+                    dy = value_sep(pi.y, pj.y, g.periodic[1], g.L[1], g.halfL[1]);
+                    if (DIM == 3) dz = value_sep(pi.z, pj.z, g.periodic[2], g.L[2], g.halfL[2]);
+                    f(j, pj, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (uint32_t j = a; j < b; ++j) {
+                const float4 pj = __ldg(P.spos + j);
+                float dx, dy, dz;
+                const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz);
+                if (d2 < r2 && j != s) f(j, pj, dx, dy, dz, d2);
+            }
+        }
+    });
+}
+
+// Batched visit.  The predicate loop tests up to 32 consecutive candidates
+// of a segment and records acceptances in a per-lane bit mask; the mask is
+// then drained with body(j, pj, dx, dy, dz, d2), positions reloaded (an L1
+// hit) and value separations recomputed.  With ~15% of candidates accepted,
+// evaluating the body inside the predicate loop would make the whole warp pay
+// for a body on nearly every iteration; draining per batch costs the warp
+// max-over-lanes(popcount) bodies per batch instead, and needs no shared
+// memory (so occupancy and L1 capacity for the neighbour loads are kept).
+// The self pair is removed from the mask once per batch, not per candidate.
+template <int DIM, bool GENERAL, class B>
+__device__ __forceinline__ void visit_pairs_batched(const PairParams& P, uint32_t s,
+                                                    const float4& pi, B&& body) {
+    const Geom& g = P.g;
+    const float r2 = g.r2;
+    for_each_segment<DIM, GENERAL>(P, pi, [&](uint32_t a, uint32_t b, float sx, float sy,
+                                              float sz) {
+        const bool shifted = GENERAL || sx != 0.0f || sy != 0.0f || sz != 0.0f;
+#pragma unroll 1
+        for (uint32_t j0 = a; j0 < b; j0 += 32) {
+            const uint32_t cnt = min(b - j0, 32u);
+            uint32_t m = 0;
+            if (shifted) {
+#pragma unroll 1
+                for (uint32_t k = 0; k < cnt; ++k) {
+                    const float4 pj = __ldg(P.spos + j0 + k);
+                    float dx, dy, dz;
+                    const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz);
+                    if (d2 < r2) m |= 1u << k;
+                }
+            } else {
+#pragma unroll 4
+                for (uint32_t k = 0; k < cnt; ++k) {
+                    const float4 pj = __ldg(P.spos + j0 + k);
+                    float dx, dy, dz;
+                    const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz);
+                    if (d2 < r2) m |= 1u << k;
+                }
+            }
+            if (s - j0 < cnt) m &= ~(1u << (s - j0));
+            while (m) {
+                const uint32_t k = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t j = j0 + k;
+                const float4 pj = __ldg(P.spos + j);
+                float dx, dy, dz;
+                if (shifted) {
+                    dx = value_sep(pi.x, pj.x, g.periodic[0], g.L[0], g.halfL[0]);
+                    dy = value_sep(pi.y, pj.y, g.periodic[1], g.L[1], g.halfL[1]);
+                    dz = DIM == 3 ? value_sep(pi.z, pj.z, g.periodic[2], g.L[2], g.halfL[2]) : 0.0f;
+                } else {
+                    dx = __fsub_rn(pj.x, pi.x);
+                    dy = __fsub_rn(pj.y, pi.y);
+                    dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
+                }
+                body(j, pj, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            }
+        }
+    });
+}
+
 // FP64 block sum of one value per thread into partial[blockIdx.x].
+template <int THREADS>
 __device__ __forceinline__ void block_partial(double v, double* partial) {
-    __shared__ double s_red[kPairThreads / 32];
+    __shared__ double s_red[THREADS / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
@@ -203,86 +287,95 @@ __device__ __forceinline__ void block_partial(double v, double* partial) {
     if (threadIdx.x == 0) {
         double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < kPairThreads / 32; ++w) t += s_red[w];
+        for (int w = 0; w < THREADS / 32; ++w) t += s_red[w];
         partial[blockIdx.x] = t;
     }
 }
 
+// Forward for the cheap operators (COUNT, GAUSS): direct visit.
 template <int DIM, bool GENERAL, int OP>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
+    if (s >= P.n) return;
+    const float4 pi = __ldg(P.spos + s);
+    float a0 = 0.0f;
+    visit_pairs<DIM, GENERAL>(P, s, pi,
+        [&](uint32_t j, const float4&, float, float, float, float d2) {
+            if (OP == AB_OP_COUNT) a0 += 1.0f;
+            else a0 += __ldg(&P.sv[j].x) * ex2_approx(-P.s_log2e * d2);
+        });
+    o.out[__ldg(P.perm + s)] = a0;
+}
+
+// Forward for LJ / EXPF / SOFT: direct visit (measured faster than the
+// batched drain for these short bodies).
+template <int DIM, bool GENERAL, int OP>
+__global__ void __launch_bounds__(kPairThreads, 8)
+k_pair_fwd_q(PairParams P, PairOut o) {
+    const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
+    const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
+        [&](uint32_t, const float4&, float dx, float dy, float dz, float d2) {
+            if (OP == AB_OP_LJ) {
+                const float sr2 = P.sig2 * rcp_approx(d2);
+                const float sr6 = sr2 * sr2 * sr2;
+                a0 = fmaf(sr6, sr6 - 1.0f, a0);
+            } else if (d2 > 0.0f) {   // EXPF, SOFT: coincident points contribute 0
+                const float inv_d = rsqrt_approx(d2);
+                const float d = d2 * inv_d;
+                const float mag = (OP == AB_OP_EXPF) ? -P.c * ex2_approx(-kLog2e * d) * inv_d
+                                                     : -P.k * (P.r - d) * inv_d;
+                a0 = fmaf(mag, dx, a0);
+                a1 = fmaf(mag, dy, a1);
+                a2 = fmaf(mag, dz, a2);
+            }
+        });
     if (live) {
-        const float4 pi = __ldg(P.spos + s);
-        visit_pairs<DIM, GENERAL>(P, s, pi,
-            [&](uint32_t j, const float4& pj, float dx, float dy, float dz, float d2) {
-                if (OP == AB_OP_COUNT) {
-                    a0 += 1.0f;
-                } else if (OP == AB_OP_GAUSS) {
-                    a0 += __ldg(&P.sv[j].x) * ex2_approx(-P.s_log2e * d2);
-                } else if (OP == AB_OP_LJ) {
-                    float sr2 = P.sig2 * rcp_approx(d2);
-                    float sr6 = sr2 * sr2 * sr2;
-                    a0 += sr6 * (sr6 - 1.0f);
-                } else {  // EXPF, SOFT: vector forces, skip coincident points
-                    if (d2 > 0.0f) {
-                        float inv_d = rsqrt_approx(d2);
-                        float d = d2 * inv_d;
-                        float mag = (OP == AB_OP_EXPF)
-                                        ? -P.c * ex2_approx(-kLog2e * d) * inv_d
-                                        : -P.k * (P.r - d) * inv_d;
-                        a0 += mag * dx;
-                        a1 += mag * dy;
-                        a2 += mag * dz;
-                    }
-                }
-            });
         const uint32_t p = __ldg(P.perm + s);
-        if (OP == AB_OP_COUNT || OP == AB_OP_GAUSS) {
-            o.out[p] = a0;
-        } else if (OP == AB_OP_LJ) {
+        if (OP == AB_OP_LJ) {
             a0 *= 0.5f * P.eps;
             o.out[p] = a0;
         } else {
             o.out4[p] = make_float4(a0, a1, DIM == 3 ? a2 : 0.0f, 0.0f);
         }
     }
-    if (OP == AB_OP_LJ && o.partial) block_partial(live ? (double)a0 : 0.0, o.partial);
+    if (OP == AB_OP_LJ && o.partial) block_partial<kPairThreads>(live ? (double)a0 : 0.0, o.partial);
 }
 
+// Adjoints (GAUSS, LJ): batched visit.
 template <int DIM, bool GENERAL, int OP>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_bwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
+    const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 vi = live ? __ldg(P.sv + s) : make_float2(0.f, 0.f);
     float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f;
-    float2 vi = make_float2(0.0f, 0.0f);
+    if (live) visit_pairs_batched<DIM, GENERAL>(P, s, pi,
+        [&](uint32_t j, const float4&, float dx, float dy, float dz, float d2) {
+            const float2 vj = __ldg(P.sv + j);
+            if (OP == AB_OP_GAUSS) {
+                const float k = ex2_approx(-P.s_log2e * d2);
+                const float coef = fmaf(vi.y, vj.x, vj.y * vi.x) * k;
+                gx = fmaf(coef, dx, gx);
+                gy = fmaf(coef, dy, gy);
+                gz = fmaf(coef, dz, gz);
+                dw = fmaf(vj.y, k, dw);
+                ds = fmaf(vj.x * k, d2, ds);
+            } else {  // LJ: 1/2 (g_i + g_j) eps (12 sr12 - 6 sr6) / d2
+                const float inv = rcp_approx(d2);
+                const float sr2 = P.sig2 * inv;
+                const float sr6 = sr2 * sr2 * sr2;
+                const float coef = (vi.y + vj.y) * (sr6 * fmaf(6.0f, sr6, -3.0f)) * inv;
+                gx = fmaf(coef, dx, gx);
+                gy = fmaf(coef, dy, gy);
+                gz = fmaf(coef, dz, gz);
+            }
+        });
     if (live) {
-        const float4 pi = __ldg(P.spos + s);
-        vi = __ldg(P.sv + s);
-        visit_pairs<DIM, GENERAL>(P, s, pi,
-            [&](uint32_t j, const float4& pj, float dx, float dy, float dz, float d2) {
-                const float2 vj = __ldg(P.sv + j);
-                if (OP == AB_OP_GAUSS) {
-                    float k = ex2_approx(-P.s_log2e * d2);
-                    float coef = (vi.y * vj.x + vj.y * vi.x) * k;
-                    gx += coef * dx;
-                    gy += coef * dy;
-                    gz += coef * dz;
-                    dw += vj.y * k;
-                    ds += vj.x * k * d2;
-                } else {  // LJ: 1/2 (g_i + g_j) eps (12 sr12 - 6 sr6) / d2
-                    float inv = rcp_approx(d2);
-                    float sr2 = P.sig2 * inv;
-                    float sr6 = sr2 * sr2 * sr2;
-                    float coef = (vi.y + vj.y) * (sr6 * (6.0f * sr6 - 3.0f)) * inv;
-                    gx += coef * dx;
-                    gy += coef * dy;
-                    gz += coef * dz;
-                }
-            });
         const uint32_t p = __ldg(P.perm + s);
         if (OP == AB_OP_GAUSS) {
             const float two_s = 2.0f * P.s;
@@ -290,18 +383,16 @@ k_pair_bwd(PairParams P, PairOut o) {
                 o.grad_pos[p] = make_float4(two_s * gx, two_s * gy,
                                             DIM == 3 ? two_s * gz : 0.0f, 0.0f);
             if (o.grad_w) o.grad_w[p] = dw;
-        } else {
-            if (o.grad_pos)
-                o.grad_pos[p] = make_float4(P.eps * gx, P.eps * gy,
-                                            DIM == 3 ? P.eps * gz : 0.0f, 0.0f);
+        } else if (o.grad_pos) {
+            o.grad_pos[p] = make_float4(P.eps * gx, P.eps * gy, DIM == 3 ? P.eps * gz : 0.0f, 0.0f);
         }
     }
     if (OP == AB_OP_GAUSS && o.partial)
-        block_partial(live ? -(double)vi.y * (double)ds : 0.0, o.partial);
+        block_partial<kPairThreads>(live ? -(double)vi.y * (double)ds : 0.0, o.partial);
 }
 
 template <int DIM, bool GENERAL>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
@@ -313,7 +404,7 @@ k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
 }
 
 template <int DIM, bool GENERAL>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_emit(PairParams P, const int64_t* __restrict__ offsets, int32_t* __restrict__ idx) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
@@ -349,16 +440,16 @@ int pair_grid(int64_t n) { return (int)((n + kPairThreads - 1) / kPairThreads); 
 
 #define COMMA_OP(x) , x
 
-#define AB_DISPATCH_DG(KERNEL, OPARGS, ...)                                          \
-    do {                                                                             \
-        const int grid = pair_grid(cl.n);                                            \
-        if (cl.g.dim == 3) {                                                         \
-            if (cl.g.general) KERNEL<3, true OPARGS><<<grid, kPairThreads, 0, st>>>(__VA_ARGS__); \
-            else KERNEL<3, false OPARGS><<<grid, kPairThreads, 0, st>>>(__VA_ARGS__);  \
-        } else {                                                                     \
-            if (cl.g.general) KERNEL<2, true OPARGS><<<grid, kPairThreads, 0, st>>>(__VA_ARGS__); \
-            else KERNEL<2, false OPARGS><<<grid, kPairThreads, 0, st>>>(__VA_ARGS__);  \
-        }                                                                            \
+#define AB_DISPATCH_DG(KERNEL, THREADS, OPARGS, ...)                                  \
+    do {                                                                              \
+        const int grid = (int)((cl.n + THREADS - 1) / THREADS);                       \
+        if (cl.g.dim == 3) {                                                          \
+            if (cl.g.general) KERNEL<3, true OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
+            else KERNEL<3, false OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);       \
+        } else {                                                                      \
+            if (cl.g.general) KERNEL<2, true OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
+            else KERNEL<2, false OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);       \
+        }                                                                             \
     } while (0)
 
 cudaError_t launch_pair_fwd(const CellList& cl, ab_op op, const ab_op_params& prm,
@@ -366,11 +457,11 @@ cudaError_t launch_pair_fwd(const CellList& cl, ab_op op, const ab_op_params& pr
     if (cl.n <= 0) return cudaSuccess;
     PairParams P = make_params(cl, prm, sv);
     switch (op) {
-        case AB_OP_COUNT: AB_DISPATCH_DG(k_pair_fwd, COMMA_OP(AB_OP_COUNT), P, o); break;
-        case AB_OP_GAUSS: AB_DISPATCH_DG(k_pair_fwd, COMMA_OP(AB_OP_GAUSS), P, o); break;
-        case AB_OP_LJ: AB_DISPATCH_DG(k_pair_fwd, COMMA_OP(AB_OP_LJ), P, o); break;
-        case AB_OP_EXPF: AB_DISPATCH_DG(k_pair_fwd, COMMA_OP(AB_OP_EXPF), P, o); break;
-        case AB_OP_SOFT: AB_DISPATCH_DG(k_pair_fwd, COMMA_OP(AB_OP_SOFT), P, o); break;
+        case AB_OP_COUNT: AB_DISPATCH_DG(k_pair_fwd, kPairThreads, COMMA_OP(AB_OP_COUNT), P, o); break;
+        case AB_OP_GAUSS: AB_DISPATCH_DG(k_pair_fwd, kPairThreads, COMMA_OP(AB_OP_GAUSS), P, o); break;
+        case AB_OP_LJ: AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_LJ), P, o); break;
+        case AB_OP_EXPF: AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_EXPF), P, o); break;
+        case AB_OP_SOFT: AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_SOFT), P, o); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -381,8 +472,8 @@ cudaError_t launch_pair_bwd(const CellList& cl, ab_op op, const ab_op_params& pr
     if (cl.n <= 0) return cudaSuccess;
     PairParams P = make_params(cl, prm, sv);
     switch (op) {
-        case AB_OP_GAUSS: AB_DISPATCH_DG(k_pair_bwd, COMMA_OP(AB_OP_GAUSS), P, o); break;
-        case AB_OP_LJ: AB_DISPATCH_DG(k_pair_bwd, COMMA_OP(AB_OP_LJ), P, o); break;
+        case AB_OP_GAUSS: AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_GAUSS), P, o); break;
+        case AB_OP_LJ: AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_LJ), P, o); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -392,7 +483,7 @@ cudaError_t launch_pair_count(const CellList& cl, uint32_t* counts, cudaStream_t
     if (cl.n <= 0) return cudaSuccess;
     ab_op_params prm{};
     PairParams P = make_params(cl, prm, nullptr);
-    AB_DISPATCH_DG(k_pair_count, , P, counts);
+    AB_DISPATCH_DG(k_pair_count, kPairThreads, , P, counts);
     return cudaGetLastError();
 }
 
@@ -401,7 +492,7 @@ cudaError_t launch_pair_emit(const CellList& cl, const int64_t* offsets, int32_t
     if (cl.n <= 0) return cudaSuccess;
     ab_op_params prm{};
     PairParams P = make_params(cl, prm, nullptr);
-    AB_DISPATCH_DG(k_pair_emit, , P, offsets, idx);
+    AB_DISPATCH_DG(k_pair_emit, kPairThreads, , P, offsets, idx);
     return cudaGetLastError();
 }
 

@@ -96,9 +96,17 @@ def test_argument_errors(ab, ctx):
     with pytest.raises(ab.AbError) as e:          # output aliases the weights
         ab.ab_pair_sum(ctx, "gauss", ab.OpParams(s=1.0), w=wt, out=wt)
     assert e.value.status == 2
-    with pytest.raises(ab.AbError) as e:          # output aliases the positions
-        ab.ab_pair_sum(ctx, "expf", ab.OpParams(c=1.0), out=pos)
+    g = dev(synth.weights(w.n, 2))
+    gpos = torch.empty((w.n, 4), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(ab.AbError) as e:          # gradient output aliases grad_out
+        ab.ab_pair_sum_bwd(ctx, "gauss", ab.OpParams(s=1.0), wt, g, gpos, g)
     assert e.value.status == 2
+    # the sorted copy is the library's: overwriting the caller's positions
+    # after the build is allowed and does not change the result
+    c0 = host(ab.ab_pair_sum(ctx, "count", ab.OpParams()))
+    f = ab.ab_pair_sum(ctx, "expf", ab.OpParams(c=1.0), out=pos)
+    c1 = host(ab.ab_pair_sum(ctx, "count", ab.OpParams()))
+    assert np.array_equal(c0, c1) and f.data_ptr() == pos.data_ptr()
     with pytest.raises(ab.AbError) as e:          # no adjoint for EXPF
         ab.ab_pair_sum_bwd(ctx, "expf", ab.OpParams(), None, wt)
     assert e.value.status == 7
