@@ -27,9 +27,11 @@
  *    errors are returned immediately and launch nothing.  Errors detected on
  *    the device (a wait that timed out) are latched and returned by the next
  *    ab_sync().
- *  - Outputs must not overlap inputs (the paper's aliasing rule, Sec. 2.2.3:
- *    an operator that writes what it reads goes through a temporary); an
- *    overlap returns AB_ERR_ALIAS.
+ *  - Outputs must not overlap the call's inputs (the paper's aliasing rule,
+ *    Sec. 2.2.3: an operator that writes what it reads goes through a
+ *    temporary); an overlap returns AB_ERR_ALIAS.  ab_build copies the
+ *    positions into the library's sorted workspace, so later pair sums do
+ *    not read the caller's position array and may overwrite it.
  *  - The context owns its workspace (cell table, sorted copies, scan state)
  *    and grows it on demand with cudaMalloc; AB_ERR_OOM leaves the context
  *    usable with its previous workspace.
