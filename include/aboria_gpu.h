@@ -243,6 +243,40 @@ ab_status ab_bd_step(ab_ctx* ctx, const ab_domain* dom, int64_t n,
                      float* pos4, const float* force4, float dt, float D,
                      uint64_t seed, uint64_t step);
 
+/* Allocation-free exclusive prefix sum of n uint32 values (the paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory).  out[k] = in[0] + ... + in[k-1] for 0 <= k < n, wrapping modulo
+ * 2^32; in may equal out (in place), other overlaps return AB_ERR_ALIAS.
+ * Scanning the n_cells + 1 cell counts of a cell list, the last one zero,
+ * gives the cell_start table that ab_build computes.
+ *
+ * Who needs it: code that must not call cudaMalloc or any allocating routine
+ * -- for example a caller whose device memory is entirely owned by its own
+ * pool or a framework's caching allocator (a raw cudaMalloc would bypass the
+ * pool's accounting and can synchronise the device), a real-time or
+ * embedded loop with a fixed memory budget fixed at start-up, or code that
+ * has no ab_ctx because creating one allocates.  The look-back state this
+ * scan needs lives in a file-scope __device__ array of about 32 KB that every
+ * GPU which loads the library keeps until the process exits; nothing is
+ * allocated or freed by this call.
+ *
+ *   in, out: device uint32 pointers on the current device, 4-byte aligned.
+ *   n:       0 <= n <= 16,777,216 (2^24); larger n returns
+ *            AB_ERR_INVALID_ARG.
+ *   stream:  cudaStream_t the work is issued on (NULL = legacy stream).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and resets
+ * the part it uses on its stream before the scan, so calls that overlap on
+ * the GPU (different streams, no ordering between them) race and give
+ * wrong results.  The call is asynchronous.  If a bounded device-side wait
+ * gives up (not expected in practice: it waits at most one second for a
+ * tile that is already running), out[0] is set to 0xFFFFFFFF, a value an
+ * exclusive scan never produces there.  Errors: AB_ERR_INVALID_ARG,
+ * AB_ERR_ALIAS, AB_ERR_CUDA. */
+ab_status ab_exclusive_scan_u32_static(const uint32_t* in, uint32_t* out,
+                                       int64_t n, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* ab_status_string(ab_status status);
 

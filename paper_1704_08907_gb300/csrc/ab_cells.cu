@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "ab_internal.cuh"
 
 namespace ab {
@@ -295,4 +297,92 @@ cudaError_t launch_gather_vars(const CellList& cl, const float* w, const float* 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the cell-offset scan (ab_exclusive_scan_u32_static
+// in include/aboria_gpu.h).  The look-back state lives in a file-scope
+// __device__ array instead of context workspace, so the call needs no
+// cudaMalloc and no context.  Every GPU that loads the library keeps this
+// array (about 32 KB) until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int64_t kStaticScanMaxTiles = 4096;
+constexpr int64_t kStaticScanMaxItems = kStaticScanMaxTiles * kScanTile;  // 2^24
+
+struct StaticScanScratch {
+    uint64_t status[kStaticScanMaxTiles];
+    uint32_t ticket;
+    uint32_t err;
+};
+
+static __device__ __align__(256) StaticScanScratch g_static_scan;
+
+// After the scan: a wait that gave up is reported through the output itself
+// (out[0] of an exclusive scan is always 0, so 0xFFFFFFFF there is
+// unambiguous), and the error word is cleared for the next call.
+__global__ void k_static_scan_check(uint32_t* out, uint32_t* err) {
+    if (*err) {
+        out[0] = 0xFFFFFFFFu;
+        *err = 0;
+    }
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+StaticScanScratch* g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+// Device address of g_static_scan on the current device, looked up once per
+// device.  In host code the symbol itself is only a host-side stand-in.
+static cudaError_t static_scan_scratch(StaticScanScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scan);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = (StaticScanScratch*)p;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace ab
+
+#pragma GCC visibility push(default)
+extern "C" ab_status ab_exclusive_scan_u32_static(const uint32_t* in, uint32_t* out,
+                                                  int64_t n, void* stream) {
+    if (n < 0 || n > ab::kStaticScanMaxItems) return AB_ERR_INVALID_ARG;
+    if (n == 0) return AB_OK;
+    if (!in || !out || ((uintptr_t)in & 3u) || ((uintptr_t)out & 3u)) return AB_ERR_INVALID_ARG;
+    const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out, nb = (uintptr_t)n * 4u;
+    if (a0 != b0 && a0 < b0 + nb && b0 < a0 + nb) return AB_ERR_ALIAS;  // partial overlap
+    ab::StaticScanScratch* sc = nullptr;
+    cudaError_t e = ab::static_scan_scratch(&sc);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return AB_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t tiles = ab::scan_tiles(n);
+    // the array keeps the previous call's contents: reset what must start at 0
+    e = cudaMemsetAsync(sc->status, 0, tiles * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sc->ticket, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) {
+        ab::k_scan<uint32_t><<<(unsigned)tiles, ab::kThreads, 0, st>>>(
+            in, out, n, sc->status, &sc->ticket, &sc->err, -1, ab::kScanLimitNs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        ab::k_static_scan_check<<<1, 1, 0, st>>>(out, &sc->err);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return AB_ERR_CUDA;
+    }
+    return AB_OK;
+}
+#pragma GCC visibility pop
