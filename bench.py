@@ -41,6 +41,11 @@ SM_MAX_MHZ = 2070.0
 OPS_PER_CANDIDATE = 9
 OPS_PER_PAIR_LJ_BWD = 12
 OPS_PER_PAIR_LJ_FWD = 7
+# DRAM traffic of one k_pair_bwd<3,false,LJ> launch on this workload, from an
+# ncu --set full capture (dram__bytes_read.sum + dram__bytes_write.sum:
+# 30.81 MB + 0.94 MB), valid only for the kernel source it was taken on.
+TRAFFIC_BWD_BYTES = 31.75e6
+TRAFFIC_SOURCE_SHA = "d1685f495e1f9e13"
 
 
 def peaks():
@@ -245,6 +250,9 @@ def run_ours(args, rank, world):
         e2e_ms += e0.elapsed_time(e1)
     ab.ab_sync(ctx)
 
+    import hashlib
+    src = os.path.join(ROOT, "paper_1704_08907_gb300", "csrc", "ab_pairs.cu")
+    same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC_SOURCE_SHA
     pk, pk_kind = peaks()
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
     bwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_BWD
@@ -265,7 +273,9 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,LJ>",
                      "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak,
+                     "traffic": TRAFFIC_BWD_BYTES if same_kernel else None,
+                     "algorithmic_ops_per_launch": bwd_ops,
                      "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"},
         "phases_ms": {"build": float(np.mean(t_build)), "fwd": float(np.mean(t_fwd)),
                       "bwd": float(np.mean(t_bwd))},
@@ -301,8 +311,8 @@ def oracle_sample(w, nq, seed=17):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--oracle-queries", type=int, default=131072)
     args = ap.parse_args()

@@ -310,7 +310,8 @@ void or_cells_list(const or_cells *cl, int64_t nq, const int64_t *queries,
 /* pos64: float64[n][4]; w: float64[n] (GAUSS) or NULL; out: float64[nq][4] */
 /* (scalar ops write out[q][0]).  prm = {s, eps, sigma, c, k, r}.           */
 /* absmode != 0 sums |term| (componentwise; for LJ the two halves of the    */
-/* potential are added in magnitude) -- the denominator of the error metric. */
+/* potential, for SOFT the k r and k d parts, are added in magnitude) -- the */
+/* denominator of the error metric.                                         */
 /* ------------------------------------------------------------------------ */
 
 /* FP64 separation with the image chosen by the FP32 rule. */
@@ -357,6 +358,9 @@ void or_pair_eval(int op, int absmode, const double *prm, int dim,
                 if (d2 > 0) {
                     double d = sqrt(d2);
                     double mag = (op == 3) ? -c * exp(-d) : -kk * (r - d);
+                    /* k (r - d) cancels near the cut-off: the error metric
+                     * counts the k r and k d parts in magnitude */
+                    if (absmode && op == 4) mag = kk * (r + d);
                     for (int k = 0; k < dim; ++k) t[k] = mag * dx[k] / d;
                 }
             }

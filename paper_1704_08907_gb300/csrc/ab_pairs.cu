@@ -324,10 +324,15 @@ k_pair_fwd_q(PairParams P, PairOut o) {
                 const float sr6 = sr2 * sr2 * sr2;
                 a0 = fmaf(sr6, sr6 - 1.0f, a0);
             } else if (d2 > 0.0f) {   // EXPF, SOFT: coincident points contribute 0
-                const float inv_d = rsqrt_approx(d2);
-                const float d = d2 * inv_d;
-                const float mag = (OP == AB_OP_EXPF) ? -P.c * ex2_approx(-kLog2e * d) * inv_d
-                                                     : -P.k * (P.r - d) * inv_d;
+                float mag;
+                if (OP == AB_OP_EXPF) {
+                    const float inv_d = rsqrt_approx(d2);
+                    mag = -P.c * ex2_approx(-kLog2e * (d2 * inv_d)) * inv_d;
+                } else {
+                    // r - d cancels near the cut-off: take d correctly rounded
+                    const float d = __fsqrt_rn(d2);
+                    mag = __fdiv_rn(-P.k * (P.r - d), d);
+                }
                 a0 = fmaf(mag, dx, a0);
                 a1 = fmaf(mag, dy, a1);
                 a2 = fmaf(mag, dz, a2);
