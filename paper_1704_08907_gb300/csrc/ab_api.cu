@@ -222,7 +222,7 @@ ab_status ab_destroy(ab_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_id, c->cl.rank, c->cl.tmp,
                     c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
-                    c->sc.partial, c->sc.counts};
+                    c->sc.partial, c->sc.counts, c->sc.dense_ws};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -250,6 +250,8 @@ ab_status ab_sync(ab_ctx* c) {
         cudaMemset(c->d_err, 0, sizeof(uint32_t));
         if (h & ab::DEVERR_SCAN_TIMEOUT)
             return fail(c, AB_ERR_TIMEOUT, "scan look-back wait exceeded its time limit");
+        if (h & ab::DEVERR_TC_TIMEOUT)
+            return fail(c, AB_ERR_TIMEOUT, "tensor-core pipeline wait exceeded its time limit");
     }
     return AB_OK;
 }
@@ -473,8 +475,18 @@ ab_status ab_kernel_matvec(ab_ctx* c, int64_t m, int64_t n, const float* X, cons
         overlaps(out, ob, W, (size_t)n * nrhs * 4))
         return fail(c, AB_ERR_ALIAS, "out overlaps an input");
     cudaSetDevice(c->device);
-    cudaError_t e = ab::launch_dense_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s,
-                                         prec, out, c->stream);
+    cudaError_t e;
+    if (prec == AB_PREC_FP32) {
+        e = ab::launch_dense_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, out,
+                                 c->stream);
+    } else {
+        if (nrhs != 64 || (prec != AB_PREC_BF16X3 && prec != AB_PREC_BF16))
+            return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths: BF16X3 / BF16 with nrhs == 64");
+        e = grow(&c->sc.dense_ws, &c->sc.cap_dense_ws, ab::dense_tc_workspace_bytes(n), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_matvec workspace");
+        e = ab::launch_dense_tc_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, out,
+                                    c->sc.dense_ws, c->d_err, c->stream);
+    }
     if (e == cudaErrorNotSupported)
         return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");
     return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "ab_kernel_matvec");
@@ -508,8 +520,26 @@ ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, 
         partial = c->sc.partial;
     }
     int pc = 0;
-    cudaError_t e = ab::launch_dense_bwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec,
-                                         G, dW, (float4*)dX, (float4*)dY, partial, &pc, c->stream);
+    cudaError_t e;
+    if (prec == AB_PREC_FP32) {
+        e = ab::launch_dense_bwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, G, dW,
+                                 (float4*)dX, (float4*)dY, partial, &pc, c->stream);
+    } else {
+        if (nrhs != 64 || (prec != AB_PREC_BF16X3 && prec != AB_PREC_BF16))
+            return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths: BF16X3 / BF16 with nrhs == 64");
+        // dW = K(Y, X) G on the tensor cores; dX, dY, ds on CUDA cores
+        e = cudaSuccess;
+        if (dW && n > 0) {
+            e = grow(&c->sc.dense_ws, &c->sc.cap_dense_ws, ab::dense_tc_workspace_bytes(m), c->stream);
+            if (e == cudaSuccess)
+                e = ab::launch_dense_tc_fwd(n, m, (const float4*)Y, (const float4*)X, nrhs, G, s, prec,
+                                            dW, c->sc.dense_ws, c->d_err, c->stream);
+        }
+        if (e == cudaSuccess)
+            e = ab::launch_dense_bwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s,
+                                     AB_PREC_FP32, G, nullptr, (float4*)dX, (float4*)dY, partial, &pc,
+                                     c->stream);
+    }
     if (e == cudaErrorNotSupported)
         return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_matvec_bwd");

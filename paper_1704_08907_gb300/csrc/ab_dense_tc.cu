@@ -1,0 +1,469 @@
+// Dense kernel operator out = K(X, Y) W on the tcgen05 tensor cores
+// (RBF / Gaussian-process operators, paper Sec. 1 and Sec. 1.1; dense global
+// operators, Sec. 2.2.2).
+//
+// One CTA per 128 rows of X, looping over tiles of 128 Y points:
+//   epilogue warps 0-3  thread = row i (= TMEM lane i): d2 = |x_i - y_j|^2 in
+//                       FP32 by direct differences, p = exp(-s d2) with ex2,
+//                       p split into bf16 p_hi + p_lo, both written to TMEM
+//                       with tcgen05.st (the A operand of the next MMA);
+//   warp 4 (one thread) tcgen05.mma kind::f16, A = P from TMEM, B = W tile
+//                       from shared memory, FP32 accumulator D[128 x 64] in
+//                       TMEM: D += P_hi W_hi + P_hi W_lo + P_lo W_hi
+//                       (AB_PREC_BF16X3; AB_PREC_BF16 keeps P_hi W_hi only);
+//   warp 5 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
+// W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
+// tile by tile in exactly the shared-memory image the MMA reads (K-major,
+// 128-byte swizzle), so each tile arrives by one contiguous bulk copy.
+// The P buffers are double-buffered so the epilogue of tile t+1 overlaps the
+// MMAs of tile t.  The exponentials (MUFU) and the split are the bound, as in
+// a softmax-free attention forward.
+//
+// Every wait is bounded: a role that waits longer than kWaitLimitNs raises
+// the CTA's abort flag and the device error word, every role leaves its loop,
+// the MMA warp waits (bounded) for its issued MMAs, the producer for its
+// copies, and the TMEM is freed before the CTA exits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ab_internal.cuh"
+
+namespace ab {
+
+namespace {
+
+constexpr int kTM = 128;            // rows of X per CTA (= TMEM lanes)
+constexpr int kTN = 128;            // Y points per tile (= MMA K per tile)
+constexpr int kRhs = 64;            // MMA N
+constexpr int kStages = 3;          // W ring depth
+constexpr int kTileBytes = kRhs * kTN * 2;          // one bf16 matrix: 16 KB
+constexpr int kStageBytes = 2 * kTileBytes;         // hi + lo
+constexpr int kThreadsTC = 192;     // 4 epilogue warps + MMA warp + producer warp
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColD = 0;       // D: columns [0, 64)
+constexpr uint32_t kColP = 128;     // P buffer b: hi at 128 + 128 b, lo at +64
+constexpr long long kWaitLimitNs = 2000000000ll;
+constexpr float kLog2eTC = 1.4426950408889634f;
+
+struct SmemLayout {
+    // W ring first: each stage must be 1024-byte aligned for the swizzle atoms
+    static constexpr int w = 0;
+    static constexpr int bars = kStages * kStageBytes;          // 96 KB
+    static constexpr int full = bars;                           // [kStages]
+    static constexpr int empty = full + 8 * kStages;            // [kStages]
+    static constexpr int pfull = empty + 8 * kStages;           // [2]
+    static constexpr int pempty = pfull + 16;                   // [2]
+    static constexpr int accfull = pempty + 16;
+    static constexpr int tmem_slot = accfull + 8;
+    static constexpr int abort_flag = tmem_slot + 4;
+    static constexpr int bytes = abort_flag + 4;
+};
+// + alignment slack; rounded up past half of the SM's 228 KB so that only
+// one CTA is resident per SM (each CTA allocates all 512 TMEM columns)
+constexpr int kSmemBytes = 120 * 1024;
+static_assert(SmemLayout::bytes + 1024 <= kSmemBytes, "shared memory layout");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ long long gtimer() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on a phase parity.  Returns false if this CTA aborted (here or
+// in another role); raises the abort flag and the device error on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          uint32_t* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            atomicOr(err, DEVERR_TC_TIMEOUT);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::f16 (bf16 inputs, fp32 accumulate)
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused here): 16 B
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                  // version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major,
+// N = 64, M = 128.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kRhs >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ float ex2f_tc(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// Two floats -> packed bf16x2 (lo element in the low half), round to nearest.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float bf16lo_to_f(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16hi_to_f(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+// ---------------------------------------------------------------------------
+// W -> tile-native bf16 hi/lo images.  Tile t (points 128 t .. 128 t + 127)
+// occupies 32 KB: hi image then lo image, each 64 rows (right-hand sides) x
+// 128 points, stored as two 8 KB K-blocks of 64 points; inside a K-block,
+// row n is 128 bytes at (n / 8) * 1024 + (n % 8) * 128 with its 16-byte
+// chunk c stored at chunk c ^ (n % 8) (the 128-byte swizzle).  One thread
+// writes one 16-byte chunk (8 points) of one row of both images.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
+         uint8_t* __restrict__ img) {
+    const int64_t total = tiles * kRhs * (kTN / 8);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int chunk = (int)(e % (kTN / 8));          // 0..15 along points
+        const int row = (int)((e / (kTN / 8)) % kRhs);   // right-hand side
+        const int64_t t = e / (kTN / 8 * kRhs);
+        const int kb = chunk / 8, c = chunk % 8;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t j = t * kTN + chunk * 8 + 2 * q + h;
+                v[h] = (j < n && row < nrhs) ? __ldg(W + j * nrhs + row) : 0.0f;
+            }
+            hi[q] = pack_bf16x2(v[0], v[1]);
+            lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
+        }
+        const int64_t off = kb * 8192 + (row / 8) * 1024 + (row % 8) * 128 + ((c ^ (row % 8)) * 16);
+        uint8_t* base = img + t * (int64_t)kStageBytes;
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(base + kTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
+// Y padded to whole tiles; padding points sit far away so their kernel
+// values underflow to exactly 0.
+__global__ void __launch_bounds__(256)
+k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, float4* __restrict__ Yp) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad;
+         j += (int64_t)gridDim.x * blockDim.x)
+        Yp[j] = j < n ? __ldg(Y + j) : make_float4(1e15f, 1e15f, 1e15f, 0.0f);
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
+               const float4* __restrict__ Yp, const uint8_t* __restrict__ wimg, float ns_log2e,
+               float* __restrict__ out, uint32_t* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar_full = sbase + SmemLayout::full;
+    const uint32_t bar_empty = sbase + SmemLayout::empty;
+    const uint32_t bar_pfull = sbase + SmemLayout::pfull;
+    const uint32_t bar_pempty = sbase + SmemLayout::pempty;
+    const uint32_t bar_acc = sbase + SmemLayout::accfull;
+    uint32_t* tmem_slot = (uint32_t*)(smem + SmemLayout::tmem_slot);
+    volatile int* abort_flag = (volatile int*)(smem + SmemLayout::abort_flag);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_pfull + 8 * b, 128);
+            mbar_init(bar_pempty + 8 * b, 1);
+        }
+        mbar_init(bar_acc, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         sbase + SmemLayout::tmem_slot),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t row0 = (int64_t)blockIdx.x * kTM;
+
+    if (warp == 5) {
+        // ---------------- producer: W tiles into the ring ----------------
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t t = 0; t < tiles; ++t) {
+                const int s = (int)(t % kStages);
+                const uint32_t use = (uint32_t)(t / kStages);
+                if (t >= kStages && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, abort_flag, err))
+                    break;
+                mbar_arrive_expect_tx(bar_full + 8 * s, kStageBytes);
+                bulk_copy(sbase + SmemLayout::w + s * kStageBytes, wimg + t * (int64_t)kStageBytes,
+                          kStageBytes, bar_full + 8 * s);
+                issued = t + 1;
+            }
+            // copies still in flight must land before the CTA may exit
+            for (int64_t t = issued > kStages ? issued - kStages : 0; t < issued; ++t) {
+                const int s = (int)(t % kStages);
+                const long long t0 = gtimer();
+                while (!mbar_try_wait(bar_full + 8 * s, (uint32_t)(t / kStages) & 1)) {
+                    if (gtimer() - t0 > kWaitLimitNs) {
+                        atomicOr(err, DEVERR_TC_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 4) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            for (int64_t t = 0; t < tiles; ++t) {
+                const int s = (int)(t % kStages);
+                const int b = (int)(t & 1);
+                if (!mbar_wait(bar_full + 8 * s, (uint32_t)(t / kStages) & 1, abort_flag, err)) break;
+                if (!mbar_wait(bar_pfull + 8 * b, (uint32_t)(t >> 1) & 1, abort_flag, err)) break;
+                tc_fence_after();
+                const uint32_t a_hi = tmem + kColP + 128 * b;
+                const uint32_t a_lo = a_hi + 64;
+                const uint32_t w_hi = sbase + SmemLayout::w + s * kStageBytes;
+                const uint32_t w_lo = w_hi + kTileBytes;
+#pragma unroll
+                for (int ks = 0; ks < kTN / 16; ++ks) {
+                    const uint32_t boff = (ks / 4) * 8192 + (ks % 4) * 32;
+                    const uint32_t acol = ks * 8;   // 16 bf16 = 8 columns
+                    mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_hi + boff), kIdescBf16,
+                           (t > 0 || ks > 0) ? 1u : 0u);
+                    if (SPLIT) {
+                        mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_lo + boff), kIdescBf16, 1u);
+                        mma_ts(tmem + kColD, a_lo + acol, sw128_desc(w_hi + boff), kIdescBf16, 1u);
+                    }
+                }
+                tc_commit(bar_empty + 8 * s);
+                tc_commit(bar_pempty + 8 * b);
+            }
+            // always signal the epilogue; after an abort it only waits for the
+            // MMAs already issued before freeing TMEM
+            tc_commit(bar_acc);
+        }
+    } else {
+        // ---------------- epilogue warps 0-3: row i = thread ----------------
+        const int i = threadIdx.x;   // TMEM lane of this thread
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        float4 xi = make_float4(1e15f, -1e15f, 1e15f, 0.f);   // padding row: K = 0
+        if (row0 + i < m) xi = __ldg(X + row0 + i);
+        for (int64_t t = 0; t < tiles; ++t) {
+            const int b = (int)(t & 1);
+            if (t >= 2) {
+                const bool ok = mbar_wait(bar_pempty + 8 * b, (uint32_t)((t - 2) >> 1) & 1, abort_flag, err);
+                if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
+            }
+            tc_fence_after();
+            const float4* yt = Yp + t * kTN;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kTN; c0 += 32) {
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float p[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float4 y = __ldg(yt + c0 + 2 * q + h);
+                        const float dx = xi.x - y.x, dy = xi.y - y.y, dz = xi.z - y.z;
+                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        p[h] = ex2f_tc(ns_log2e * d2);
+                    }
+                    hi[q] = pack_bf16x2(p[0], p[1]);
+                    lo[q] = pack_bf16x2(p[0] - bf16lo_to_f(hi[q]), p[1] - bf16hi_to_f(hi[q]));
+                }
+                const uint32_t col = kColP + 128 * b + c0 / 2;
+                tmem_st16(lane_base + col, hi);
+                if (SPLIT) tmem_st16(lane_base + col + 64, lo);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(bar_pfull + 8 * b);
+        }
+        // accumulator ready (or aborted: the wait is still bounded)
+        bool ok = mbar_wait(bar_acc, 0, abort_flag, err);
+        ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld needs the whole warp
+        tc_fence_after();
+        if (ok) {
+            float* orow = out + (row0 + i) * kRhs;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kRhs; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(lane_base + kColD + c0, v);
+                tmem_wait_ld();
+                if (row0 + i < m) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4*>(orow + c0 + q) =
+                            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                        __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                }
+            }
+        }
+    }
+    // The MMA thread's final commit arrives on bar_acc once its MMAs are done;
+    // make sure that has happened (bounded) before TMEM is released.
+    if (warp == 4 && lane == 0) {
+        const long long t0 = gtimer();
+        while (!mbar_try_wait(bar_acc, 0)) {
+            if (gtimer() - t0 > kWaitLimitNs) {
+                atomicOr(err, DEVERR_TC_TIMEOUT);
+                break;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
+}  // namespace
+
+size_t dense_tc_workspace_bytes(int64_t n) {
+    const int64_t tiles = (n + kTN - 1) / kTN;
+    return (size_t)tiles * kStageBytes + (size_t)tiles * kTN * 16 + 256;
+}
+
+cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,
+                                const float* W, float s, ab_prec prec, float* out, void* ws,
+                                uint32_t* err, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    if (nrhs != kRhs || (prec != AB_PREC_BF16X3 && prec != AB_PREC_BF16))
+        return cudaErrorNotSupported;
+    const int64_t tiles = (n + kTN - 1) / kTN;
+    if (tiles == 0) return cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st);
+    uint8_t* wimg = (uint8_t*)ws;                                    // 1024-aligned (cudaMalloc)
+    float4* Yp = (float4*)(wimg + (size_t)tiles * kStageBytes);
+    const int64_t prep_items = tiles * kRhs * (kTN / 8);
+    k_prep_w<<<(unsigned)((prep_items + 255) / 256 < 4096 ? (prep_items + 255) / 256 : 4096), 256, 0,
+               st>>>(n, nrhs, W, tiles, wimg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_prep_y<<<(unsigned)((tiles * kTN + 255) / 256), 256, 0, st>>>(n, Y, tiles * kTN, Yp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((m + kTM - 1) / kTM);
+    const float ns = -s * kLog2eTC;
+    if (prec == AB_PREC_BF16X3) {
+        static bool attr = false;
+        if (!attr) {
+            e = cudaFuncSetAttribute(k_dense_tc_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_dense_tc_fwd<true><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yp, wimg, ns, out, err);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            e = cudaFuncSetAttribute(k_dense_tc_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_dense_tc_fwd<false><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yp, wimg, ns, out, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ab

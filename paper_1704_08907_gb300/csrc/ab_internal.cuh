@@ -13,6 +13,7 @@ namespace ab {
 // Device-side error bits latched in the context's error word.
 enum : uint32_t {
     DEVERR_SCAN_TIMEOUT = 1u,
+    DEVERR_TC_TIMEOUT = 2u,   // a tensor-core kernel's pipeline wait gave up
 };
 
 // Cell-lattice geometry of one build, passed by value to kernels.
@@ -65,6 +66,8 @@ struct Scratch {
     size_t cap_partial = 0;
     uint32_t* counts = nullptr;       // pair-list counts (user order)
     size_t cap_counts = 0;
+    uint8_t* dense_ws = nullptr;      // tensor-core operand images
+    size_t cap_dense_ws = 0;
 };
 
 // ---- launchers (defined in the .cu files) ----------------------------------
@@ -123,6 +126,12 @@ AB_HIDDEN cudaError_t launch_dense_bwd(int64_t m, int64_t n, const float4* X,
                                        double* partial, int* partial_count,
                                        cudaStream_t st);
 AB_HIDDEN int dense_partial_capacity(int64_t m, int64_t n);
+
+// ab_dense_tc.cu (tcgen05 path; nrhs must be 64)
+AB_HIDDEN size_t dense_tc_workspace_bytes(int64_t n);
+AB_HIDDEN cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y,
+                                          int nrhs, const float* W, float s, ab_prec prec,
+                                          float* out, void* ws, uint32_t* err, cudaStream_t st);
 
 // ab_bd.cu
 AB_HIDDEN cudaError_t launch_bd_step(const Geom& g, int64_t n, float4* pos,
