@@ -294,6 +294,93 @@ def run_ours(args, rank, world):
     return out, w
 
 
+def _timed(fn, reps, flush=None):
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def also_dense(reps=5):
+    """Dense kernel operator, 65,536 x 65,536 x 64 right-hand sides: FP32 CUDA
+    cores vs the tcgen05 paths (TFLOP/s counts 2 M N nrhs per product)."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    d = synth.c4()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X = torch.from_numpy(synth.pack4(d.X)).to(dev)
+    Y = torch.from_numpy(synth.pack4(d.Y)).to(dev)
+    W = torch.from_numpy(d.W).to(dev)
+    m, n, nrhs = X.shape[0], Y.shape[0], W.shape[1]
+    ctx = ab.Context(dev.index)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    outs, res = {}, {}
+    for prec in ("fp32", "bf16x3", "bf16"):
+        out = torch.empty((m, nrhs), dtype=torch.float32, device=dev)
+        fn = lambda: ab.ab_kernel_matvec(ctx, X, Y, W, d.s, prec, out=out)  # noqa: E731
+        for _ in range(2):
+            fn()
+        ms = _timed(fn, reps, flush)
+        res[prec] = {"ms": ms, "tflops": 2.0 * m * n * nrhs / (ms * 1e-3) / 1e12}
+        outs[prec] = out
+    ab.ab_sync(ctx)
+    ref = outs["fp32"].double()
+    scale = ref.abs().max().item()
+    for prec in ("bf16x3", "bf16"):
+        res[prec]["max_abs_diff_vs_fp32_path_over_max"] = \
+            float((outs[prec].double() - ref).abs().max().item() / scale)
+    res["speedup_bf16x3_vs_fp32"] = res["fp32"]["ms"] / res["bf16x3"]["ms"]
+    res["exps"] = m * n
+    res["workload"] = "X, Y 65,536 points in [0,1]^3, W 65,536 x 64, Gaussian kernel l = 0.1"
+    ctx.close()
+    return res
+
+
+def also_c3(reps=5):
+    """Clustered 16.7M-point workload: rebuild + Gaussian pair sum + adjoint
+    (x, w, s); pairs per second."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    w = synth.c3()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pos = torch.from_numpy(w.pos).to(dev)
+    wt = torch.from_numpy(w.w).to(dev)
+    g = torch.from_numpy(w.g).to(dev)
+    ctx = ab.Context(dev.index)
+    dom = ab.Domain(3, w.periodic, w.radius)
+    prm = ab.OpParams(s=w.params["s"])
+    y = torch.empty(w.n, dtype=torch.float32, device=dev)
+    gpos = torch.empty((w.n, 4), dtype=torch.float32, device=dev)
+    gw = torch.empty(w.n, dtype=torch.float32, device=dev)
+    gs = torch.empty((), dtype=torch.float64, device=dev)
+    ab.ab_build(ctx, dom, pos)
+    pairs = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
+
+    def step():
+        ab.ab_build(ctx, dom, pos)
+        ab.ab_pair_sum(ctx, "gauss", prm, w=wt, out=y)
+        ab.ab_pair_sum_bwd(ctx, "gauss", prm, wt, g, gpos, gw, gs)
+
+    for _ in range(2):
+        step()
+    ms = _timed(step, reps)
+    ab.ab_sync(ctx)
+    ctx.close()
+    return {"workload": "16,777,216 points in 1024 Gaussian blobs, periodic cube, "
+                        f"r={w.radius:.7f} (64 neighbours mean): rebuild + gauss fwd + adjoint",
+            "pairs_per_step": pairs, "ms_per_step": ms,
+            "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True}
+
+
 def oracle_sample(w, nq, seed=17):
     """Oracle LJ energy + adjoint over nq query particles (cell list over all)."""
     import oracle
@@ -315,6 +402,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--oracle-queries", type=int, default=131072)
+    ap.add_argument("--no-also", action="store_true",
+                    help="skip the secondary 16.7M-point and dense-operator measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -351,6 +440,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     out, w = run_ours(args, rank, world)
+    if rank == 0 and not args.no_also and world == 1:
+        out["also"] = {"c3_clustered_16M": also_c3(), "dense_kernel_matvec": also_dense()}
     if rank == 0:
         pairs, secs, cores = oracle_sample(w, args.oracle_queries)
         out["cpu_baseline"] = {"value": pairs / secs, "unit": UNIT, "cores": cores,

@@ -3,15 +3,19 @@
 // operators, Sec. 2.2.2).
 //
 // One CTA per 128 rows of X, looping over tiles of 128 Y points:
-//   epilogue warps 0-3  thread = row i (= TMEM lane i): d2 = |x_i - y_j|^2 in
-//                       FP32 by direct differences, p = exp(-s d2) with ex2,
-//                       p split into bf16 p_hi + p_lo, both written to TMEM
-//                       with tcgen05.st (the A operand of the next MMA);
-//   warp 4 (one thread) tcgen05.mma kind::f16, A = P from TMEM, B = W tile
+//   epilogue warps 0-7  warp w serves rows 32 (w % 4) .. +31 (its TMEM lane
+//                       quadrant) and columns 64 (w / 4) .. +63 of each tile,
+//                       so two warps per scheduler hide MUFU/FMA latency;
+//                       thread = row i: the base-2 exponent -s log2(e) d2 in
+//                       the centred expanded form (see k_prep_y: 3 FMA + 1 add
+//                       per element), p = ex2 of it, p split into
+//                       bf16 p_hi + p_lo, both written to TMEM with
+//                       tcgen05.st (the A operand of the next MMA);
+//   warp 8 (one thread) tcgen05.mma kind::f16, A = P from TMEM, B = W tile
 //                       from shared memory, FP32 accumulator D[128 x 64] in
 //                       TMEM: D += P_hi W_hi + P_hi W_lo + P_lo W_hi
 //                       (AB_PREC_BF16X3; AB_PREC_BF16 keeps P_hi W_hi only);
-//   warp 5 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
+//   warp 9 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
 // W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
 // tile by tile in exactly the shared-memory image the MMA reads (K-major,
 // 128-byte swizzle), so each tile arrives by one contiguous bulk copy.
@@ -39,7 +43,8 @@ constexpr int kRhs = 64;            // MMA N
 constexpr int kStages = 3;          // W ring depth
 constexpr int kTileBytes = kRhs * kTN * 2;          // one bf16 matrix: 16 KB
 constexpr int kStageBytes = 2 * kTileBytes;         // hi + lo
-constexpr int kThreadsTC = 192;     // 4 epilogue warps + MMA warp + producer warp
+constexpr int kEpiWarps = 8;        // two warps per TMEM lane quadrant (column halves)
+constexpr int kThreadsTC = 32 * (kEpiWarps + 2);   // + MMA warp + producer warp
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColD = 0;       // D: columns [0, 64)
 constexpr uint32_t kColP = 128;     // P buffer b: hi at 128 + 128 b, lo at +64
@@ -230,20 +235,76 @@ k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
     }
 }
 
-// Y padded to whole tiles; padding points sit far away so their kernel
-// values underflow to exactly 0.
+// Order-independent float min/max through their sortable integer images.
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// Bounding box of Y (bbox[0..2] = min, bbox[4..6] = max, as ordered ints;
+// initialised by the caller to (0xFFFFFFFF, 0)).
 __global__ void __launch_bounds__(256)
-k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, float4* __restrict__ Yp) {
+k_bbox(int64_t n, const float4* __restrict__ Y, uint32_t* __restrict__ bbox) {
+    uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0u, 0u, 0u};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const float4 y = __ldg(Y + j);
+        const float v[3] = {y.x, y.y, y.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = min(mn[k], f2ord(v[k]));
+            mx[k] = max(mx[k], f2ord(v[k]));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = min(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = max(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(bbox + k, mn[k]);
+            atomicMax(bbox + 4 + k, mx[k]);
+        }
+    }
+}
+
+// Per Y point, centred on c = bounding-box midpoint:
+//   yhat = (2 s' (y - c), -s' |y - c|^2),  s' = s log2(e)
+// so that for a row x the exponent of K in base 2 is
+//   x~ . yhat.xyz + yhat.w - s' |x~|^2 = -s' |x - y|^2,   x~ = x - c.
+// Centring keeps every term below s' * (half-diagonal^2) in magnitude, so the
+// FP32 rounding of the expanded form stays ~1e-5 in the exponent.  Padding
+// points get yhat = (0, 0, 0, -inf): their kernel values are exactly 0.
+__global__ void __launch_bounds__(256)
+k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* __restrict__ bbox,
+         float sl2e, float4* __restrict__ Yhat, float4* __restrict__ centre) {
+    const float c0 = 0.5f * (ord2f(bbox[0]) + ord2f(bbox[4]));
+    const float c1 = 0.5f * (ord2f(bbox[1]) + ord2f(bbox[5]));
+    const float c2 = 0.5f * (ord2f(bbox[2]) + ord2f(bbox[6]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *centre = make_float4(c0, c1, c2, 0.0f);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad;
-         j += (int64_t)gridDim.x * blockDim.x)
-        Yp[j] = j < n ? __ldg(Y + j) : make_float4(1e15f, 1e15f, 1e15f, 0.0f);
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (j < n) {
+            const float4 y = __ldg(Y + j);
+            const float a = y.x - c0, b = y.y - c1, c = y.z - c2;
+            const float nrm = fmaf(c, c, fmaf(b, b, a * a));
+            Yhat[j] = make_float4(2.0f * sl2e * a, 2.0f * sl2e * b, 2.0f * sl2e * c, -sl2e * nrm);
+        } else {
+            Yhat[j] = make_float4(0.0f, 0.0f, 0.0f, -__int_as_float(0x7f800000));
+        }
+    }
 }
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
-               const float4* __restrict__ Yp, const uint8_t* __restrict__ wimg, float ns_log2e,
-               float* __restrict__ out, uint32_t* __restrict__ err) {
+               const float4* __restrict__ Yhat, const float4* __restrict__ centre,
+               const uint8_t* __restrict__ wimg, float sl2e, float* __restrict__ out,
+               uint32_t* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
@@ -262,14 +323,14 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
             mbar_init(bar_empty + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(bar_pfull + 8 * b, 128);
+            mbar_init(bar_pfull + 8 * b, 32 * kEpiWarps);
             mbar_init(bar_pempty + 8 * b, 1);
         }
         mbar_init(bar_acc, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          sbase + SmemLayout::tmem_slot),
                      "r"(kTmemCols)
@@ -282,7 +343,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
     const uint32_t tmem = *tmem_slot;
     const int64_t row0 = (int64_t)blockIdx.x * kTM;
 
-    if (warp == 5) {
+    if (warp == kEpiWarps + 1) {
         // ---------------- producer: W tiles into the ring ----------------
         if (lane == 0) {
             int64_t issued = 0;
@@ -308,7 +369,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
                 }
             }
         }
-    } else if (warp == 4) {
+    } else if (warp == kEpiWarps) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             for (int64_t t = 0; t < tiles; ++t) {
@@ -340,11 +401,19 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
             tc_commit(bar_acc);
         }
     } else {
-        // ---------------- epilogue warps 0-3: row i = thread ----------------
-        const int i = threadIdx.x;   // TMEM lane of this thread
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        float4 xi = make_float4(1e15f, -1e15f, 1e15f, 0.f);   // padding row: K = 0
-        if (row0 + i < m) xi = __ldg(X + row0 + i);
+        // ---------------- epilogue warps: row i, one column half ----------------
+        const int quad = warp & 3, half = warp >> 2;
+        const int i = quad * 32 + lane;   // TMEM lane = row of this thread
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        // row in centred coordinates; a padding row gets -inf: K = 0
+        float xa = 0.f, xb = 0.f, xc = 0.f, ci = -__int_as_float(0x7f800000);
+        if (row0 + i < m) {
+            const float4 x = __ldg(X + row0 + i), c = __ldg(centre);
+            xa = x.x - c.x;
+            xb = x.y - c.y;
+            xc = x.z - c.z;
+            ci = -sl2e * fmaf(xc, xc, fmaf(xb, xb, xa * xa));
+        }
         for (int64_t t = 0; t < tiles; ++t) {
             const int b = (int)(t & 1);
             if (t >= 2) {
@@ -352,9 +421,9 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
                 if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
             }
             tc_fence_after();
-            const float4* yt = Yp + t * kTN;
+            const float4* yt = Yhat + t * kTN + half * (kTN / 2);
 #pragma unroll 1
-            for (int c0 = 0; c0 < kTN; c0 += 32) {
+            for (int c0 = 0; c0 < kTN / 2; c0 += 32) {
                 uint32_t hi[16], lo[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -362,14 +431,13 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const float4 y = __ldg(yt + c0 + 2 * q + h);
-                        const float dx = xi.x - y.x, dy = xi.y - y.y, dz = xi.z - y.z;
-                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        p[h] = ex2f_tc(ns_log2e * d2);
+                        const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
+                        p[h] = ex2f_tc(e);
                     }
                     hi[q] = pack_bf16x2(p[0], p[1]);
                     lo[q] = pack_bf16x2(p[0] - bf16lo_to_f(hi[q]), p[1] - bf16hi_to_f(hi[q]));
                 }
-                const uint32_t col = kColP + 128 * b + c0 / 2;
+                const uint32_t col = kColP + 128 * b + (half * (kTN / 2) + c0) / 2;
                 tmem_st16(lane_base + col, hi);
                 if (SPLIT) tmem_st16(lane_base + col + 64, lo);
             }
@@ -384,7 +452,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
         if (ok) {
             float* orow = out + (row0 + i) * kRhs;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kRhs; c0 += 16) {
+            for (int c0 = half * (kRhs / 2); c0 < (half + 1) * (kRhs / 2); c0 += 16) {
                 uint32_t v[16];
                 tmem_ld16(lane_base + kColD + c0, v);
                 tmem_wait_ld();
@@ -400,7 +468,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
     }
     // The MMA thread's final commit arrives on bar_acc once its MMAs are done;
     // make sure that has happened (bounded) before TMEM is released.
-    if (warp == 4 && lane == 0) {
+    if (warp == kEpiWarps && lane == 0) {
         const long long t0 = gtimer();
         while (!mbar_try_wait(bar_acc, 0)) {
             if (gtimer() - t0 > kWaitLimitNs) {
@@ -412,7 +480,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 4)
+    if (warp == kEpiWarps)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols)
                      : "memory");
@@ -422,7 +490,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
 
 size_t dense_tc_workspace_bytes(int64_t n) {
     const int64_t tiles = (n + kTN - 1) / kTN;
-    return (size_t)tiles * kStageBytes + (size_t)tiles * kTN * 16 + 256;
+    return (size_t)tiles * kStageBytes + (size_t)tiles * kTN * 16 + 16 + 32 + 256;
 }
 
 cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,
@@ -434,16 +502,23 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
     const int64_t tiles = (n + kTN - 1) / kTN;
     if (tiles == 0) return cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st);
     uint8_t* wimg = (uint8_t*)ws;                                    // 1024-aligned (cudaMalloc)
-    float4* Yp = (float4*)(wimg + (size_t)tiles * kStageBytes);
+    float4* Yhat = (float4*)(wimg + (size_t)tiles * kStageBytes);
+    float4* centre = Yhat + tiles * kTN;
+    uint32_t* bbox = (uint32_t*)(centre + 1);
     const int64_t prep_items = tiles * kRhs * (kTN / 8);
     k_prep_w<<<(unsigned)((prep_items + 255) / 256 < 4096 ? (prep_items + 255) / 256 : 4096), 256, 0,
                st>>>(n, nrhs, W, tiles, wimg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_prep_y<<<(unsigned)((tiles * kTN + 255) / 256), 256, 0, st>>>(n, Y, tiles * kTN, Yp);
+    if ((e = cudaMemsetAsync(bbox, 0xFF, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bbox + 4, 0x00, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const float sl2e = s * kLog2eTC;
+    k_prep_y<<<(unsigned)((tiles * kTN + 255) / 256), 256, 0, st>>>(n, Y, tiles * kTN, bbox, sl2e,
+                                                                     Yhat, centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned grid = (unsigned)((m + kTM - 1) / kTM);
-    const float ns = -s * kLog2eTC;
     if (prec == AB_PREC_BF16X3) {
         static bool attr = false;
         if (!attr) {
@@ -452,7 +527,8 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_dense_tc_fwd<true><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yp, wimg, ns, out, err);
+        k_dense_tc_fwd<true><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg, sl2e,
+                                                                   out, err);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -461,7 +537,8 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_dense_tc_fwd<false><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yp, wimg, ns, out, err);
+        k_dense_tc_fwd<false><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg, sl2e,
+                                                                    out, err);
     }
     return cudaGetLastError();
 }
