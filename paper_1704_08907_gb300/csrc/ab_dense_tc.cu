@@ -3,19 +3,19 @@
 // operators, Sec. 2.2.2).
 //
 // One CTA per 128 rows of X, looping over tiles of 128 Y points:
-//   epilogue warps 0-7  warp w serves rows 32 (w % 4) .. +31 (its TMEM lane
-//                       quadrant) and columns 64 (w / 4) .. +63 of each tile,
-//                       so two warps per scheduler hide MUFU/FMA latency;
+//   epilogue warps 0-15 warp w serves rows 32 (w % 4) .. +31 (its TMEM lane
+//                       quadrant) and columns 32 (w / 4) .. +31 of each tile,
+//                       so four warps per scheduler hide MUFU/FMA latency;
 //                       thread = row i: the base-2 exponent -s log2(e) d2 in
 //                       the centred expanded form (see k_prep_y: 3 FMA + 1 add
 //                       per element), p = ex2 of it, p split into
 //                       bf16 p_hi + p_lo, both written to TMEM with
 //                       tcgen05.st (the A operand of the next MMA);
-//   warp 8 (one thread) tcgen05.mma kind::f16, A = P from TMEM, B = W tile
+//   warp 16 (one thread) tcgen05.mma kind::f16, A = P from TMEM, B = W tile
 //                       from shared memory, FP32 accumulator D[128 x 64] in
 //                       TMEM: D += P_hi W_hi + P_hi W_lo + P_lo W_hi
 //                       (AB_PREC_BF16X3; AB_PREC_BF16 keeps P_hi W_hi only);
-//   warp 9 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
+//   warp 17 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
 // W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
 // tile by tile in exactly the shared-memory image the MMA reads (K-major,
 // 128-byte swizzle), so each tile arrives by one contiguous bulk copy.
@@ -35,6 +35,8 @@
 
 namespace ab {
 
+extern int g_num_sms;
+
 namespace {
 
 constexpr int kTM = 128;            // rows of X per CTA (= TMEM lanes)
@@ -42,8 +44,11 @@ constexpr int kTN = 128;            // Y points per tile (= MMA K per tile)
 constexpr int kRhs = 64;            // MMA N
 constexpr int kStages = 3;          // W ring depth
 constexpr int kTileBytes = kRhs * kTN * 2;          // one bf16 matrix: 16 KB
-constexpr int kStageBytes = 2 * kTileBytes;         // hi + lo
-constexpr int kEpiWarps = 8;        // two warps per TMEM lane quadrant (column halves)
+constexpr int kImgBytes = 2 * kTileBytes;           // hi + lo images of one W tile
+constexpr int kYBytes = kTN * 16;                   // yhat of one tile
+constexpr int kStageBytes = kImgBytes + kYBytes;    // 34 KB, a multiple of 1024
+constexpr int kEpiWarps = 16;       // four warps per TMEM lane quadrant (column quarters)
+constexpr int kColsPerWarp = kTN / (kEpiWarps / 4);   // 32 columns of each tile
 constexpr int kThreadsTC = 32 * (kEpiWarps + 2);   // + MMA warp + producer warp
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColD = 0;       // D: columns [0, 64)
@@ -54,7 +59,7 @@ constexpr float kLog2eTC = 1.4426950408889634f;
 struct SmemLayout {
     // W ring first: each stage must be 1024-byte aligned for the swizzle atoms
     static constexpr int w = 0;
-    static constexpr int bars = kStages * kStageBytes;          // 96 KB
+    static constexpr int bars = kStages * kStageBytes;          // 102 KB
     static constexpr int full = bars;                           // [kStages]
     static constexpr int empty = full + 8 * kStages;            // [kStages]
     static constexpr int pfull = empty + 8 * kStages;           // [2]
@@ -68,6 +73,7 @@ struct SmemLayout {
 // one CTA is resident per SM (each CTA allocates all 512 TMEM columns)
 constexpr int kSmemBytes = 120 * 1024;
 static_assert(SmemLayout::bytes + 1024 <= kSmemBytes, "shared memory layout");
+static_assert(kStageBytes % 1024 == 0, "stages keep the 1024-byte swizzle alignment");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -150,6 +156,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         "r"(v[15])
         : "memory");
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -229,7 +241,7 @@ k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
             lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
         }
         const int64_t off = kb * 8192 + (row / 8) * 1024 + (row % 8) * 128 + ((c ^ (row % 8)) * 16);
-        uint8_t* base = img + t * (int64_t)kStageBytes;
+        uint8_t* base = img + t * (int64_t)kImgBytes;
         *reinterpret_cast<uint4*>(base + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4*>(base + kTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
@@ -301,10 +313,15 @@ k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* 
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
+k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                const float4* __restrict__ Yhat, const float4* __restrict__ centre,
                const uint8_t* __restrict__ wimg, float sl2e, float* __restrict__ out,
                uint32_t* __restrict__ err) {
+    // blockIdx.y selects a contiguous range of Y tiles; with gridDim.y == 2
+    // the two partial sums are added into a zeroed output (0 + a + b is the
+    // same in either order, so the result stays deterministic)
+    const int64_t t_begin = total_tiles * blockIdx.y / gridDim.y;
+    const int64_t tiles = total_tiles * (blockIdx.y + 1) / gridDim.y - t_begin;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
@@ -320,7 +337,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(bar_full + 8 * s, 1);
-            mbar_init(bar_empty + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1 + kEpiWarps);   // MMA commit + one per epilogue warp
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar_pfull + 8 * b, 32 * kEpiWarps);
@@ -352,9 +369,12 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
                 const uint32_t use = (uint32_t)(t / kStages);
                 if (t >= kStages && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, abort_flag, err))
                     break;
+                const int64_t gt = t_begin + t;
                 mbar_arrive_expect_tx(bar_full + 8 * s, kStageBytes);
-                bulk_copy(sbase + SmemLayout::w + s * kStageBytes, wimg + t * (int64_t)kStageBytes,
-                          kStageBytes, bar_full + 8 * s);
+                bulk_copy(sbase + SmemLayout::w + s * kStageBytes, wimg + gt * (int64_t)kImgBytes,
+                          kImgBytes, bar_full + 8 * s);
+                bulk_copy(sbase + SmemLayout::w + s * kStageBytes + kImgBytes, Yhat + gt * kTN, kYBytes,
+                          bar_full + 8 * s);
                 issued = t + 1;
             }
             // copies still in flight must land before the CTA may exit
@@ -402,7 +422,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
         }
     } else {
         // ---------------- epilogue warps: row i, one column half ----------------
-        const int quad = warp & 3, half = warp >> 2;
+        const int quad = warp & 3, part = warp >> 2;   // lane quadrant, column slice
         const int i = quad * 32 + lane;   // TMEM lane = row of this thread
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         // row in centred coordinates; a padding row gets -inf: K = 0
@@ -420,30 +440,38 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
                 const bool ok = mbar_wait(bar_pempty + 8 * b, (uint32_t)((t - 2) >> 1) & 1, abort_flag, err);
                 if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
             }
+            const int st = (int)(t % kStages);
+            {
+                const bool ok = mbar_wait(bar_full + 8 * st, (uint32_t)(t / kStages) & 1, abort_flag, err);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
             tc_fence_after();
-            const float4* yt = Yhat + t * kTN + half * (kTN / 2);
+            const float4* yt = reinterpret_cast<const float4*>(smem + SmemLayout::w + st * kStageBytes +
+                                                               kImgBytes) + part * kColsPerWarp;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kTN / 2; c0 += 32) {
-                uint32_t hi[16], lo[16];
+            for (int c0 = 0; c0 < kColsPerWarp; c0 += 16) {
+                uint32_t hi[8], lo[8];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
+                for (int q = 0; q < 8; ++q) {
                     float p[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float4 y = __ldg(yt + c0 + 2 * q + h);
+                        const float4 y = yt[c0 + 2 * q + h];
                         const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
                         p[h] = ex2f_tc(e);
                     }
                     hi[q] = pack_bf16x2(p[0], p[1]);
                     lo[q] = pack_bf16x2(p[0] - bf16lo_to_f(hi[q]), p[1] - bf16hi_to_f(hi[q]));
                 }
-                const uint32_t col = kColP + 128 * b + (half * (kTN / 2) + c0) / 2;
-                tmem_st16(lane_base + col, hi);
-                if (SPLIT) tmem_st16(lane_base + col + 64, lo);
+                const uint32_t col = kColP + 128 * b + (part * kColsPerWarp + c0) / 2;
+                tmem_st8(lane_base + col, hi);
+                if (SPLIT) tmem_st8(lane_base + col + 64, lo);
             }
             tmem_wait_st();
             tc_fence_before();
             mbar_arrive(bar_pfull + 8 * b);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_empty + 8 * st);   // this warp is done with yhat
         }
         // accumulator ready (or aborted: the wait is still bounded)
         bool ok = mbar_wait(bar_acc, 0, abort_flag, err);
@@ -452,16 +480,18 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
         if (ok) {
             float* orow = out + (row0 + i) * kRhs;
 #pragma unroll 1
-            for (int c0 = half * (kRhs / 2); c0 < (half + 1) * (kRhs / 2); c0 += 16) {
+            for (int c0 = part * (kRhs / 4); c0 < (part + 1) * (kRhs / 4); c0 += 16) {
                 uint32_t v[16];
                 tmem_ld16(lane_base + kColD + c0, v);
                 tmem_wait_ld();
                 if (row0 + i < m) {
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4)
-                        *reinterpret_cast<float4*>(orow + c0 + q) =
-                            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
-                                        __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                    for (int q = 0; q < 16; q += 4) {
+                        const float4 r = make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                                     __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                        if (gridDim.y == 1) *reinterpret_cast<float4*>(orow + c0 + q) = r;
+                        else atomicAdd(reinterpret_cast<float4*>(orow + c0 + q), r);
+                    }
                 }
             }
         }
@@ -490,7 +520,7 @@ k_dense_tc_fwd(int64_t m, int64_t tiles, const float4* __restrict__ X,
 
 size_t dense_tc_workspace_bytes(int64_t n) {
     const int64_t tiles = (n + kTN - 1) / kTN;
-    return (size_t)tiles * kStageBytes + (size_t)tiles * kTN * 16 + 16 + 32 + 256;
+    return (size_t)tiles * kImgBytes + (size_t)tiles * kTN * 16 + 16 + 32 + 256;
 }
 
 cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,
@@ -502,7 +532,7 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
     const int64_t tiles = (n + kTN - 1) / kTN;
     if (tiles == 0) return cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st);
     uint8_t* wimg = (uint8_t*)ws;                                    // 1024-aligned (cudaMalloc)
-    float4* Yhat = (float4*)(wimg + (size_t)tiles * kStageBytes);
+    float4* Yhat = (float4*)(wimg + (size_t)tiles * kImgBytes);
     float4* centre = Yhat + tiles * kTN;
     uint32_t* bbox = (uint32_t*)(centre + 1);
     const int64_t prep_items = tiles * kRhs * (kTN / 8);
@@ -518,7 +548,13 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
     k_prep_y<<<(unsigned)((tiles * kTN + 255) / 256), 256, 0, st>>>(n, Y, tiles * kTN, bbox, sl2e,
                                                                      Yhat, centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((m + kTM - 1) / kTM);
+    const int64_t mblocks = (m + kTM - 1) / kTM;
+    // split the Y range in two when the row blocks alone leave a ragged last
+    // wave (fewer than four waves of one CTA per SM)
+    const int split = (mblocks < 4 * (int64_t)g_num_sms && tiles >= 2) ? 2 : 1;
+    if (split == 2 && (e = cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st)) != cudaSuccess)
+        return e;
+    const dim3 grid((unsigned)mblocks, (unsigned)split);
     if (prec == AB_PREC_BF16X3) {
         static bool attr = false;
         if (!attr) {
