@@ -324,7 +324,7 @@ def also_dense(reps=5):
     ctx = ab.Context(dev.index)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     outs, res = {}, {}
-    for prec in ("fp32", "bf16x3", "bf16"):
+    for prec in ("fp32", "bf16x3", "bf16", "tf32x3", "tf32"):
         out = torch.empty((m, nrhs), dtype=torch.float32, device=dev)
         fn = lambda: ab.ab_kernel_matvec(ctx, X, Y, W, d.s, prec, out=out)  # noqa: E731
         for _ in range(2):
@@ -335,10 +335,11 @@ def also_dense(reps=5):
     ab.ab_sync(ctx)
     ref = outs["fp32"].double()
     scale = ref.abs().max().item()
-    for prec in ("bf16x3", "bf16"):
+    for prec in ("bf16x3", "bf16", "tf32x3", "tf32"):
         res[prec]["max_abs_diff_vs_fp32_path_over_max"] = \
             float((outs[prec].double() - ref).abs().max().item() / scale)
     res["speedup_bf16x3_vs_fp32"] = res["fp32"]["ms"] / res["bf16x3"]["ms"]
+    res["speedup_tf32x3_vs_fp32"] = res["fp32"]["ms"] / res["tf32x3"]["ms"]
     res["exps"] = m * n
     res["workload"] = "X, Y 65,536 points in [0,1]^3, W 65,536 x 64, Gaussian kernel l = 0.1"
     ctx.close()

@@ -480,8 +480,8 @@ ab_status ab_kernel_matvec(ab_ctx* c, int64_t m, int64_t n, const float* X, cons
         e = ab::launch_dense_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, out,
                                  c->stream);
     } else {
-        if (nrhs != 64 || (prec != AB_PREC_BF16X3 && prec != AB_PREC_BF16))
-            return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths: BF16X3 / BF16 with nrhs == 64");
+        if (nrhs != 64)
+            return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths need nrhs == 64");
         e = grow(&c->sc.dense_ws, &c->sc.cap_dense_ws, ab::dense_tc_workspace_bytes(n), c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_matvec workspace");
         e = ab::launch_dense_tc_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, out,
@@ -525,8 +525,8 @@ ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, 
         e = ab::launch_dense_bwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, G, dW,
                                  (float4*)dX, (float4*)dY, partial, &pc, c->stream);
     } else {
-        if (nrhs != 64 || (prec != AB_PREC_BF16X3 && prec != AB_PREC_BF16))
-            return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths: BF16X3 / BF16 with nrhs == 64");
+        if (nrhs != 64)
+            return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths need nrhs == 64");
         // dW = K(Y, X) G on the tensor cores; dX, dY, ds on CUDA cores
         e = cudaSuccess;
         if (dW && n > 0) {

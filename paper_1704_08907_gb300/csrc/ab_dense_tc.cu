@@ -40,15 +40,23 @@ extern int g_num_sms;
 namespace {
 
 constexpr int kTM = 128;            // rows of X per CTA (= TMEM lanes)
-constexpr int kTN = 128;            // Y points per tile (= MMA K per tile)
 constexpr int kRhs = 64;            // MMA N
 constexpr int kStages = 3;          // W ring depth
-constexpr int kTileBytes = kRhs * kTN * 2;          // one bf16 matrix: 16 KB
+// A W tile is 64 rows x 256 bytes of K in either precision: 128 bf16 points
+// or 64 tf32 points.  Its P block is 64 TMEM columns either way.
+constexpr int kTileBytes = kRhs * 256;              // one hi or lo image: 16 KB
 constexpr int kImgBytes = 2 * kTileBytes;           // hi + lo images of one W tile
-constexpr int kYBytes = kTN * 16;                   // yhat of one tile
-constexpr int kStageBytes = kImgBytes + kYBytes;    // 34 KB, a multiple of 1024
 constexpr int kEpiWarps = 16;       // four warps per TMEM lane quadrant (column quarters)
-constexpr int kColsPerWarp = kTN / (kEpiWarps / 4);   // 32 columns of each tile
+template <bool TF32>
+struct Tile {
+    static constexpr int TN = TF32 ? 64 : 128;              // Y points per tile
+    static constexpr int YBytes = TN * 16;                   // yhat of one tile
+    static constexpr int StageBytes = kImgBytes + YBytes;    // 33 or 34 KB
+    static constexpr int ColsPerWarp = TN / (kEpiWarps / 4); // 16 or 32
+};
+constexpr int kStageBytesMax = Tile<false>::StageBytes;
+static_assert(Tile<false>::StageBytes % 1024 == 0 && Tile<true>::StageBytes % 1024 == 0,
+              "stages keep the 1024-byte swizzle alignment");
 constexpr int kThreadsTC = 32 * (kEpiWarps + 2);   // + MMA warp + producer warp
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColD = 0;       // D: columns [0, 64)
@@ -59,7 +67,7 @@ constexpr float kLog2eTC = 1.4426950408889634f;
 struct SmemLayout {
     // W ring first: each stage must be 1024-byte aligned for the swizzle atoms
     static constexpr int w = 0;
-    static constexpr int bars = kStages * kStageBytes;          // 102 KB
+    static constexpr int bars = kStages * kStageBytesMax;       // <= 102 KB
     static constexpr int full = bars;                           // [kStages]
     static constexpr int empty = full + 8 * kStages;            // [kStages]
     static constexpr int pfull = empty + 8 * kStages;           // [2]
@@ -73,7 +81,6 @@ struct SmemLayout {
 // one CTA is resident per SM (each CTA allocates all 512 TMEM columns)
 constexpr int kSmemBytes = 120 * 1024;
 static_assert(SmemLayout::bytes + 1024 <= kSmemBytes, "shared memory layout");
-static_assert(kStageBytes % 1024 == 0, "stages keep the 1024-byte swizzle alignment");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -147,6 +154,15 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+__device__ __forceinline__ void mma_ts_tf32(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -195,6 +211,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
 // N = 64, M = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kRhs >> 3) << 17) |
                                 ((uint32_t)(kTM >> 4) << 24);
+// kind::tf32: D fp32, A and B tf32 (format 2), both K-major, N = 64, M = 128.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kRhs >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
 
 __device__ __forceinline__ float ex2f_tc(float x) {
     float y;
@@ -208,37 +227,58 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return r;
 }
 __device__ __forceinline__ float bf16lo_to_f(uint32_t v) { return __uint_as_float(v << 16); }
+// fp32 -> tf32 (round to nearest, ties away), as an fp32 bit pattern
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float bf16hi_to_f(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 
 // ---------------------------------------------------------------------------
-// W -> tile-native bf16 hi/lo images.  Tile t (points 128 t .. 128 t + 127)
-// occupies 32 KB: hi image then lo image, each 64 rows (right-hand sides) x
-// 128 points, stored as two 8 KB K-blocks of 64 points; inside a K-block,
-// row n is 128 bytes at (n / 8) * 1024 + (n % 8) * 128 with its 16-byte
-// chunk c stored at chunk c ^ (n % 8) (the 128-byte swizzle).  One thread
-// writes one 16-byte chunk (8 points) of one row of both images.
+// W -> tile-native hi/lo images.  Tile t covers TN points (128 bf16 or 64
+// tf32) and occupies 32 KB: hi image then lo image, each 64 rows (right-hand
+// sides) x 256 bytes of K, stored as two 8 KB K-blocks of 128-byte rows;
+// inside a K-block, row n sits at (n / 8) * 1024 + (n % 8) * 128 with its
+// 16-byte chunk c stored at chunk c ^ (n % 8) (the 128-byte swizzle).  One
+// thread writes one 16-byte chunk of one row of both images.  bf16: hi is
+// W rounded to nearest, lo the rounded remainder; tf32 likewise with
+// cvt.rna.tf32.
 // ---------------------------------------------------------------------------
+template <bool TF32>
 __global__ void __launch_bounds__(256)
 k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
          uint8_t* __restrict__ img) {
-    const int64_t total = tiles * kRhs * (kTN / 8);
+    constexpr int TN = Tile<TF32>::TN;
+    constexpr int PTS = TF32 ? 4 : 8;                    // points per 16-byte chunk
+    const int64_t total = tiles * kRhs * 16;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int chunk = (int)(e % (kTN / 8));          // 0..15 along points
-        const int row = (int)((e / (kTN / 8)) % kRhs);   // right-hand side
-        const int64_t t = e / (kTN / 8 * kRhs);
+        const int chunk = (int)(e % 16);                 // 16-byte chunk along K
+        const int row = (int)((e / 16) % kRhs);          // right-hand side
+        const int64_t t = e / (16 * kRhs);
         const int kb = chunk / 8, c = chunk % 8;
         uint32_t hi[4], lo[4];
+        if (TF32) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t j = t * kTN + chunk * 8 + 2 * q + h;
-                v[h] = (j < n && row < nrhs) ? __ldg(W + j * nrhs + row) : 0.0f;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t j = t * TN + chunk * PTS + q;
+                const float v = (j < n && row < nrhs) ? __ldg(W + j * nrhs + row) : 0.0f;
+                hi[q] = to_tf32(v);
+                lo[q] = to_tf32(v - __uint_as_float(hi[q]));
             }
-            hi[q] = pack_bf16x2(v[0], v[1]);
-            lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t j = t * TN + chunk * PTS + 2 * q + h;
+                    v[h] = (j < n && row < nrhs) ? __ldg(W + j * nrhs + row) : 0.0f;
+                }
+                hi[q] = pack_bf16x2(v[0], v[1]);
+                lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
+            }
         }
         const int64_t off = kb * 8192 + (row / 8) * 1024 + (row % 8) * 128 + ((c ^ (row % 8)) * 16);
         uint8_t* base = img + t * (int64_t)kImgBytes;
@@ -311,7 +351,7 @@ k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* 
     }
 }
 
-template <bool SPLIT>
+template <bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                const float4* __restrict__ Yhat, const float4* __restrict__ centre,
@@ -320,6 +360,10 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
     // blockIdx.y selects a contiguous range of Y tiles; with gridDim.y == 2
     // the two partial sums are added into a zeroed output (0 + a + b is the
     // same in either order, so the result stays deterministic)
+    constexpr int kTN = Tile<TF32>::TN;
+    constexpr int kYBytes = Tile<TF32>::YBytes;
+    constexpr int kStageBytes = Tile<TF32>::StageBytes;
+    constexpr int kColsPerWarp = Tile<TF32>::ColsPerWarp;
     const int64_t t_begin = total_tiles * blockIdx.y / gridDim.y;
     const int64_t tiles = total_tiles * (blockIdx.y + 1) / gridDim.y - t_begin;
     extern __shared__ uint8_t smem_raw[];
@@ -402,15 +446,24 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 const uint32_t a_lo = a_hi + 64;
                 const uint32_t w_hi = sbase + SmemLayout::w + s * kStageBytes;
                 const uint32_t w_lo = w_hi + kTileBytes;
+                // 8 K steps of 32 bytes (16 bf16 or 8 tf32 points = 8 TMEM columns)
 #pragma unroll
-                for (int ks = 0; ks < kTN / 16; ++ks) {
+                for (int ks = 0; ks < 8; ++ks) {
                     const uint32_t boff = (ks / 4) * 8192 + (ks % 4) * 32;
-                    const uint32_t acol = ks * 8;   // 16 bf16 = 8 columns
-                    mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_hi + boff), kIdescBf16,
-                           (t > 0 || ks > 0) ? 1u : 0u);
-                    if (SPLIT) {
-                        mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_lo + boff), kIdescBf16, 1u);
-                        mma_ts(tmem + kColD, a_lo + acol, sw128_desc(w_hi + boff), kIdescBf16, 1u);
+                    const uint32_t acol = ks * 8;
+                    const uint32_t acc0 = (t > 0 || ks > 0) ? 1u : 0u;
+                    if (TF32) {
+                        mma_ts_tf32(tmem + kColD, a_hi + acol, sw128_desc(w_hi + boff), kIdescTf32, acc0);
+                        if (SPLIT) {
+                            mma_ts_tf32(tmem + kColD, a_hi + acol, sw128_desc(w_lo + boff), kIdescTf32, 1u);
+                            mma_ts_tf32(tmem + kColD, a_lo + acol, sw128_desc(w_hi + boff), kIdescTf32, 1u);
+                        }
+                    } else {
+                        mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_hi + boff), kIdescBf16, acc0);
+                        if (SPLIT) {
+                            mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_lo + boff), kIdescBf16, 1u);
+                            mma_ts(tmem + kColD, a_lo + acol, sw128_desc(w_hi + boff), kIdescBf16, 1u);
+                        }
                     }
                 }
                 tc_commit(bar_empty + 8 * s);
@@ -448,24 +501,42 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             tc_fence_after();
             const float4* yt = reinterpret_cast<const float4*>(smem + SmemLayout::w + st * kStageBytes +
                                                                kImgBytes) + part * kColsPerWarp;
-#pragma unroll 1
-            for (int c0 = 0; c0 < kColsPerWarp; c0 += 16) {
-                uint32_t hi[8], lo[8];
+            if (TF32) {
+                // 16 columns: one tf32 value per TMEM column; hi keeps the top
+                // 19 bits of p (truncation), lo = p - hi exactly (the MMA then
+                // reads lo's top 19 bits: relative error <= 2^-20 of p)
+                uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float p[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float4 y = yt[c0 + 2 * q + h];
-                        const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
-                        p[h] = ex2f_tc(e);
-                    }
-                    hi[q] = pack_bf16x2(p[0], p[1]);
-                    lo[q] = pack_bf16x2(p[0] - bf16lo_to_f(hi[q]), p[1] - bf16hi_to_f(hi[q]));
+                for (int q = 0; q < 16; ++q) {
+                    const float4 y = yt[q];
+                    const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
+                    const float p = ex2f_tc(e);
+                    hi[q] = __float_as_uint(p) & 0xFFFFE000u;
+                    lo[q] = __float_as_uint(p - __uint_as_float(hi[q]));
                 }
-                const uint32_t col = kColP + 128 * b + (part * kColsPerWarp + c0) / 2;
-                tmem_st8(lane_base + col, hi);
-                if (SPLIT) tmem_st8(lane_base + col + 64, lo);
+                const uint32_t col = kColP + 128 * b + part * kColsPerWarp;
+                tmem_st16(lane_base + col, hi);
+                if (SPLIT) tmem_st16(lane_base + col + 64, lo);
+            } else {
+#pragma unroll 1
+                for (int c0 = 0; c0 < kColsPerWarp; c0 += 16) {
+                    uint32_t hi[8], lo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float p[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float4 y = yt[c0 + 2 * q + h];
+                            const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
+                            p[h] = ex2f_tc(e);
+                        }
+                        hi[q] = pack_bf16x2(p[0], p[1]);
+                        lo[q] = pack_bf16x2(p[0] - bf16lo_to_f(hi[q]), p[1] - bf16hi_to_f(hi[q]));
+                    }
+                    const uint32_t col = kColP + 128 * b + (part * kColsPerWarp + c0) / 2;
+                    tmem_st8(lane_base + col, hi);
+                    if (SPLIT) tmem_st8(lane_base + col + 64, lo);
+                }
             }
             tmem_wait_st();
             tc_fence_before();
@@ -519,25 +590,25 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
 }  // namespace
 
 size_t dense_tc_workspace_bytes(int64_t n) {
-    const int64_t tiles = (n + kTN - 1) / kTN;
-    return (size_t)tiles * kImgBytes + (size_t)tiles * kTN * 16 + 16 + 32 + 256;
+    // sized for the tf32 tiling (64 points per 32 KB image), the larger one
+    const int64_t tiles = (n + 63) / 64;
+    return (size_t)tiles * kImgBytes + (size_t)tiles * 64 * 16 + 16 + 32 + 256;
 }
 
-cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,
-                                const float* W, float s, ab_prec prec, float* out, void* ws,
-                                uint32_t* err, cudaStream_t st) {
-    if (m <= 0) return cudaSuccess;
-    if (nrhs != kRhs || (prec != AB_PREC_BF16X3 && prec != AB_PREC_BF16))
-        return cudaErrorNotSupported;
-    const int64_t tiles = (n + kTN - 1) / kTN;
+template <bool TF32, bool SPLIT>
+static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,
+                             const float* W, float s, float* out, void* ws, uint32_t* err,
+                             cudaStream_t st) {
+    constexpr int TN = Tile<TF32>::TN;
+    const int64_t tiles = (n + TN - 1) / TN;
     if (tiles == 0) return cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st);
     uint8_t* wimg = (uint8_t*)ws;                                    // 1024-aligned (cudaMalloc)
     float4* Yhat = (float4*)(wimg + (size_t)tiles * kImgBytes);
-    float4* centre = Yhat + tiles * kTN;
+    float4* centre = Yhat + tiles * TN;
     uint32_t* bbox = (uint32_t*)(centre + 1);
-    const int64_t prep_items = tiles * kRhs * (kTN / 8);
-    k_prep_w<<<(unsigned)((prep_items + 255) / 256 < 4096 ? (prep_items + 255) / 256 : 4096), 256, 0,
-               st>>>(n, nrhs, W, tiles, wimg);
+    const int64_t prep_items = tiles * kRhs * 16;
+    k_prep_w<TF32><<<(unsigned)((prep_items + 255) / 256 < 4096 ? (prep_items + 255) / 256 : 4096), 256,
+                     0, st>>>(n, nrhs, W, tiles, wimg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bbox, 0xFF, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
@@ -545,8 +616,8 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
     k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const float sl2e = s * kLog2eTC;
-    k_prep_y<<<(unsigned)((tiles * kTN + 255) / 256), 256, 0, st>>>(n, Y, tiles * kTN, bbox, sl2e,
-                                                                     Yhat, centre);
+    k_prep_y<<<(unsigned)((tiles * TN + 255) / 256), 256, 0, st>>>(n, Y, tiles * TN, bbox, sl2e, Yhat,
+                                                                   centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t mblocks = (m + kTM - 1) / kTM;
     // split the Y range in two when the row blocks alone leave a ragged last
@@ -554,29 +625,31 @@ cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const flo
     const int split = (mblocks < 4 * (int64_t)g_num_sms && tiles >= 2) ? 2 : 1;
     if (split == 2 && (e = cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st)) != cudaSuccess)
         return e;
-    const dim3 grid((unsigned)mblocks, (unsigned)split);
-    if (prec == AB_PREC_BF16X3) {
-        static bool attr = false;
-        if (!attr) {
-            e = cudaFuncSetAttribute(k_dense_tc_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemBytes);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        k_dense_tc_fwd<true><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg, sl2e,
-                                                                   out, err);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            e = cudaFuncSetAttribute(k_dense_tc_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemBytes);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        k_dense_tc_fwd<false><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg, sl2e,
-                                                                    out, err);
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_dense_tc_fwd<TF32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
+    const dim3 grid((unsigned)mblocks, (unsigned)split);
+    k_dense_tc_fwd<TF32, SPLIT><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg,
+                                                                      sl2e, out, err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,
+                                const float* W, float s, ab_prec prec, float* out, void* ws,
+                                uint32_t* err, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    if (nrhs != kRhs) return cudaErrorNotSupported;
+    switch (prec) {
+        case AB_PREC_BF16X3: return launch_tc<false, true>(m, n, X, Y, nrhs, W, s, out, ws, err, st);
+        case AB_PREC_BF16: return launch_tc<false, false>(m, n, X, Y, nrhs, W, s, out, ws, err, st);
+        case AB_PREC_TF32X3: return launch_tc<true, true>(m, n, X, Y, nrhs, W, s, out, ws, err, st);
+        case AB_PREC_TF32: return launch_tc<true, false>(m, n, X, Y, nrhs, W, s, out, ws, err, st);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 }  // namespace ab

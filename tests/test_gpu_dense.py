@@ -122,10 +122,11 @@ def test_unsupported_precision_reports(ab, ctx):
 TC_TOL = 1e-4
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("m,n", [(128, 128), (512, 700), (129, 33), (300, 4100), (1, 1)])
-def test_tensor_core_bf16x3_forward_small(ab, ctx, m, n):
+def test_tensor_core_split_forward_small(ab, ctx, m, n, prec):
     d = synth.c4(m=m, n=n, nrhs=64, seed_offset=m + n)
-    out = host(ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "bf16x3"))
+    out = host(ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, prec))
     ab.ab_sync(ctx)
     ref = dense.matvec(d.X, d.Y, d.W, d.s)
     den = dense.matvec_abs(d.X, d.Y, d.W, d.s)
@@ -141,21 +142,22 @@ def test_tensor_core_full_size_sampled_rows(ab, ctx):
     rows = synth.query_sample(d.X.shape[0], 256, 12)
     ref = dense.matvec(d.X, d.Y, d.W, d.s, rows=rows)
     den = dense.matvec_abs(d.X, d.Y, d.W, d.s, rows=rows)
-    out3 = host(ab.ab_kernel_matvec(ctx, X, Y, W, d.s, "bf16x3"))
-    out1 = host(ab.ab_kernel_matvec(ctx, X, Y, W, d.s, "bf16"))
+    errs = {}
+    for prec in ("bf16x3", "bf16", "tf32x3", "tf32"):
+        out = host(ab.ab_kernel_matvec(ctx, X, Y, W, d.s, prec))
+        errs[prec] = np.max(np.abs(out[rows] - ref) / den)
     ab.ab_sync(ctx)
-    e3 = np.max(np.abs(out3[rows] - ref) / den)
-    e1 = np.max(np.abs(out1[rows] - ref) / den)
-    assert e3 <= TC_TOL, e3
-    assert e1 <= 1e-2, e1
-    assert e3 < e1
+    assert errs["bf16x3"] <= TC_TOL and errs["tf32x3"] <= TC_TOL, errs
+    assert errs["bf16"] <= 1e-2 and errs["tf32"] <= 1e-2, errs
+    assert errs["bf16x3"] < errs["bf16"] and errs["tf32x3"] < errs["tf32"], errs
 
 
-def test_tensor_core_adjoint_dW(ab, ctx):
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_adjoint_dW(ab, ctx, prec):
     d = synth.c4(m=3000, n=2000, nrhs=64, seed_offset=5)
     dW = torch.empty((2000, 64), dtype=torch.float32, device="cuda:0")
     dX = torch.empty((3000, 4), dtype=torch.float32, device="cuda:0")
-    ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "bf16x3", dev(d.G),
+    ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, prec, dev(d.G),
                             dW, dX, None, None)
     ab.ab_sync(ctx)
     rW = dense.grad_W(d.X, d.Y, d.G, d.s)
