@@ -152,6 +152,20 @@ def candidates_from_cells(start, ncell, periodic, dim):
     return int((counts * s).sum())
 
 
+def aggregate_ranks(units_per_step, local_ms, steps, dist, device):
+    """Weak scaling over independent replicas: every rank processed
+    ``units_per_step`` units per step; the job's time is the slowest rank's.
+    Returns (max_ms, units_all_ranks_per_second)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_per_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    max_ms = float(t.item())
+    return max_ms, float(u.item()) * steps / (max_ms * 1e-3)
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1704_08907_gb300 as ab
@@ -217,11 +231,9 @@ def run_ours(args, rank, world):
     t_step = t_build + t_fwd + t_bwd                       # ms, device time
     total_ms = float(t_step.sum())
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = pairs * world * args.steps / (total_ms * 1e-3)
+        total_ms, value = aggregate_ranks(pairs, total_ms, args.steps, dist, dev)
+    else:
+        value = pairs * args.steps / (total_ms * 1e-3)
 
     # end to end through the public API with host buffers
     pos_h = torch.from_numpy(w.pos).pin_memory()
@@ -382,6 +394,81 @@ def also_c3(reps=5):
             "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True}
 
 
+def also_bd(steps=100):
+    """2-D Brownian dynamics, 4,194,304 particles, x periodic / y reflecting,
+    soft repulsion within r = 0.002, Euler-Maruyama dt = 1e-5 with Philox
+    noise, full cell-list rebuild every step (rebuild + force + step, all on
+    the device; the loop is also captured as one CUDA graph)."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    w = synth.c5()
+    p = w.params
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pos = torch.from_numpy(w.pos).to(dev)
+    F = torch.empty_like(pos)
+    ctx = ab.Context(dev.index)
+    dom = ab.Domain(2, w.periodic, w.radius)
+    prm = ab.OpParams(k=p["k"])
+    ab.ab_build(ctx, dom, pos)
+    pairs0 = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
+    state = {"t": 0}
+
+    def one_step(t):
+        ab.ab_build(ctx, dom, pos)
+        ab.ab_pair_sum(ctx, "soft", prm, out=F)
+        ab.ab_bd_step(ctx, dom, pos, F, p["dt"], p["D"], p["seed"], t)
+
+    for _ in range(3):
+        one_step(state["t"])
+        state["t"] += 1
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one_step(state["t"])
+        state["t"] += 1
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ab.ab_sync(ctx)
+    res = {"workload": "2-D, N=4,194,304, x periodic / y reflecting, r=0.002, soft force "
+                       "k=1e4, dt=1e-5, D=1e-2, rebuild every step",
+           "steps": steps, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+           "pairs_per_step_initial": pairs0, "pairs_per_s_initial": pairs0 / (ms * 1e-3),
+           "gpu_launches_per_step": 7}
+    # the same loop as one CUDA graph (step index baked in per captured step)
+    try:
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(torch.cuda.current_stream(dev))
+        base = state["t"]
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap):
+                for k in range(10):
+                    one_step(base + k)
+        torch.cuda.current_stream(dev).wait_stream(cap)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        reps = max(1, steps // 10)
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        res["graph_ms_per_step"] = e0.elapsed_time(e1) / (reps * 10)
+        res["graph_note"] = "10 steps per graph; replays reuse the captured step indices"
+    except Exception as exc:  # capture unsupported in this configuration
+        res["graph_ms_per_step"] = None
+        res["graph_note"] = f"capture failed: {type(exc).__name__}: {exc}"[:200]
+    try:
+        ab.ab_sync(ctx)
+        ctx.close()
+    except Exception:
+        pass
+    return res
+
+
 def oracle_sample(w, nq, seed=17):
     """Oracle LJ energy + adjoint over nq query particles (cell list over all)."""
     import oracle
@@ -442,7 +529,8 @@ def main():
         dist.init_process_group("nccl")
     out, w = run_ours(args, rank, world)
     if rank == 0 and not args.no_also and world == 1:
-        out["also"] = {"c3_clustered_16M": also_c3(), "dense_kernel_matvec": also_dense()}
+        out["also"] = {"c3_clustered_16M": also_c3(), "dense_kernel_matvec": also_dense(),
+                       "brownian_4M_2d": also_bd()}
     if rank == 0:
         pairs, secs, cores = oracle_sample(w, args.oracle_queries)
         out["cpu_baseline"] = {"value": pairs / secs, "unit": UNIT, "cores": cores,
