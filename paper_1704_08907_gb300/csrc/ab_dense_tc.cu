@@ -11,16 +11,17 @@
 //                       per element), p = ex2 of it, p split into
 //                       bf16 p_hi + p_lo, both written to TMEM with
 //                       tcgen05.st (the A operand of the next MMA);
-//   warp 16 (one thread) tcgen05.mma kind::f16, A = P from TMEM, B = W tile
-//                       from shared memory, FP32 accumulator D[128 x 64] in
-//                       TMEM: D += P_hi W_hi + P_hi W_lo + P_lo W_hi
-//                       (AB_PREC_BF16X3; AB_PREC_BF16 keeps P_hi W_hi only);
+//   warp 16 (one thread) tcgen05.mma kind::f16 / kind::tf32, A = P from TMEM,
+//                       B = W tile from shared memory, FP32 accumulator in
+//                       TMEM: split paths D[128 x 128] += (P_hi + P_lo)
+//                       [W_hi | W_lo] (two N = 128 MMAs per K step; the
+//                       result is D[:, :64] + D[:, 64:]); plain paths
+//                       D[128 x 64] += P_hi W_hi;
 //   warp 17 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
 // W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
 // tile by tile in exactly the shared-memory image the MMA reads (K-major,
 // 128-byte swizzle), so each tile arrives by one contiguous bulk copy.
-// The P buffers are double-buffered so the epilogue of tile t+1 overlaps the
-// MMAs of tile t.  The exponentials (MUFU) and the split are the bound, as in
+// Three P buffers let the epilogue run up to two tiles ahead of the MMAs.  The exponentials (MUFU) and the split are the bound, as in
 // a softmax-free attention forward.
 //
 // Every wait is bounded: a role that waits longer than kWaitLimitNs raises
@@ -59,8 +60,9 @@ static_assert(Tile<false>::StageBytes % 1024 == 0 && Tile<true>::StageBytes % 10
               "stages keep the 1024-byte swizzle alignment");
 constexpr int kThreadsTC = 32 * (kEpiWarps + 2);   // + MMA warp + producer warp
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColD = 0;       // D: columns [0, 64)
+constexpr uint32_t kColD = 0;       // D: columns [0, 128) (split: [P W_hi | P W_lo])
 constexpr uint32_t kColP = 128;     // P buffer b: hi at 128 + 128 b, lo at +64
+constexpr int kPBufs = 3;           // TMEM: 128 + 3 * 128 = 512 columns
 constexpr long long kWaitLimitNs = 2000000000ll;
 constexpr float kLog2eTC = 1.4426950408889634f;
 
@@ -70,9 +72,9 @@ struct SmemLayout {
     static constexpr int bars = kStages * kStageBytesMax;       // <= 102 KB
     static constexpr int full = bars;                           // [kStages]
     static constexpr int empty = full + 8 * kStages;            // [kStages]
-    static constexpr int pfull = empty + 8 * kStages;           // [2]
-    static constexpr int pempty = pfull + 16;                   // [2]
-    static constexpr int accfull = pempty + 16;
+    static constexpr int pfull = empty + 8 * kStages;           // [kPBufs]
+    static constexpr int pempty = pfull + 8 * kPBufs;           // [kPBufs]
+    static constexpr int accfull = pempty + 8 * kPBufs;
     static constexpr int tmem_slot = accfull + 8;
     static constexpr int abort_flag = tmem_slot + 4;
     static constexpr int bytes = abort_flag + 4;
@@ -133,6 +135,13 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
+}
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
 }
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -214,6 +223,11 @@ constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)
 // kind::tf32: D fp32, A and B tf32 (format 2), both K-major, N = 64, M = 128.
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kRhs >> 3) << 17) |
                                 ((uint32_t)(kTM >> 4) << 24);
+// The same with N = 128: B = [W_hi | W_lo] stacked along N.
+constexpr uint32_t kIdescBf16N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                                    ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t kIdescTf32N128 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                                    ((uint32_t)(kTM >> 4) << 24);
 
 __device__ __forceinline__ float ex2f_tc(float x) {
     float y;
@@ -237,11 +251,12 @@ __device__ __forceinline__ float bf16hi_to_f(uint32_t v) { return __uint_as_floa
 
 // ---------------------------------------------------------------------------
 // W -> tile-native hi/lo images.  Tile t covers TN points (128 bf16 or 64
-// tf32) and occupies 32 KB: hi image then lo image, each 64 rows (right-hand
-// sides) x 256 bytes of K, stored as two 8 KB K-blocks of 128-byte rows;
-// inside a K-block, row n sits at (n / 8) * 1024 + (n % 8) * 128 with its
-// 16-byte chunk c stored at chunk c ^ (n % 8) (the 128-byte swizzle).  One
-// thread writes one 16-byte chunk of one row of both images.  bf16: hi is
+// tf32) and occupies 32 KB: two 16 KB K-blocks of 128 bytes of K each; a
+// K-block holds 128 rows, rows 0-63 the hi parts of the 64 right-hand sides
+// and rows 64-127 the lo parts, so B = [W_hi | W_lo] is one N = 128 operand.
+// Row n of a K-block sits at (n / 8) * 1024 + (n % 8) * 128 with its 16-byte
+// chunk c stored at chunk c ^ (n % 8) (the 128-byte swizzle).  One thread
+// writes one 16-byte chunk of one hi row and of its lo row.  bf16: hi is
 // W rounded to nearest, lo the rounded remainder; tf32 likewise with
 // cvt.rna.tf32.
 // ---------------------------------------------------------------------------
@@ -280,10 +295,11 @@ k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
                 lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
             }
         }
-        const int64_t off = kb * 8192 + (row / 8) * 1024 + (row % 8) * 128 + ((c ^ (row % 8)) * 16);
+        const int64_t off = kb * 16384 + (row / 8) * 1024 + (row % 8) * 128 + ((c ^ (row % 8)) * 16);
         uint8_t* base = img + t * (int64_t)kImgBytes;
         *reinterpret_cast<uint4*>(base + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(base + kTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        // the lo row 64 + row: same (row % 8), 8 row groups (8 KB) further
+        *reinterpret_cast<uint4*>(base + off + 8192) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
@@ -383,7 +399,7 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1 + kEpiWarps);   // MMA commit + one per epilogue warp
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kPBufs; ++b) {
             mbar_init(bar_pfull + 8 * b, 32 * kEpiWarps);
             mbar_init(bar_pempty + 8 * b, 1);
         }
@@ -438,31 +454,34 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         if (lane == 0) {
             for (int64_t t = 0; t < tiles; ++t) {
                 const int s = (int)(t % kStages);
-                const int b = (int)(t & 1);
+                const int b = (int)(t % kPBufs);
                 if (!mbar_wait(bar_full + 8 * s, (uint32_t)(t / kStages) & 1, abort_flag, err)) break;
-                if (!mbar_wait(bar_pfull + 8 * b, (uint32_t)(t >> 1) & 1, abort_flag, err)) break;
+                if (!mbar_wait(bar_pfull + 8 * b, (uint32_t)(t / kPBufs) & 1, abort_flag, err)) break;
                 tc_fence_after();
                 const uint32_t a_hi = tmem + kColP + 128 * b;
                 const uint32_t a_lo = a_hi + 64;
-                const uint32_t w_hi = sbase + SmemLayout::w + s * kStageBytes;
-                const uint32_t w_lo = w_hi + kTileBytes;
-                // 8 K steps of 32 bytes (16 bf16 or 8 tf32 points = 8 TMEM columns)
+                const uint32_t wb = sbase + SmemLayout::w + s * kStageBytes;
+                // 8 K steps of 32 bytes (16 bf16 or 8 tf32 points = 8 TMEM columns);
+                // split: D[:, 0:128] += (P_hi + P_lo) [W_hi | W_lo] as two N = 128
+                // MMAs (the extra P_lo W_lo term only adds accuracy)
 #pragma unroll
                 for (int ks = 0; ks < 8; ++ks) {
-                    const uint32_t boff = (ks / 4) * 8192 + (ks % 4) * 32;
+                    const uint64_t bdesc = sw128_desc(wb + (ks / 4) * 16384 + (ks % 4) * 32);
                     const uint32_t acol = ks * 8;
                     const uint32_t acc0 = (t > 0 || ks > 0) ? 1u : 0u;
                     if (TF32) {
-                        mma_ts_tf32(tmem + kColD, a_hi + acol, sw128_desc(w_hi + boff), kIdescTf32, acc0);
                         if (SPLIT) {
-                            mma_ts_tf32(tmem + kColD, a_hi + acol, sw128_desc(w_lo + boff), kIdescTf32, 1u);
-                            mma_ts_tf32(tmem + kColD, a_lo + acol, sw128_desc(w_hi + boff), kIdescTf32, 1u);
+                            mma_ts_tf32(tmem + kColD, a_hi + acol, bdesc, kIdescTf32N128, acc0);
+                            mma_ts_tf32(tmem + kColD, a_lo + acol, bdesc, kIdescTf32N128, 1u);
+                        } else {
+                            mma_ts_tf32(tmem + kColD, a_hi + acol, bdesc, kIdescTf32, acc0);
                         }
                     } else {
-                        mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_hi + boff), kIdescBf16, acc0);
                         if (SPLIT) {
-                            mma_ts(tmem + kColD, a_hi + acol, sw128_desc(w_lo + boff), kIdescBf16, 1u);
-                            mma_ts(tmem + kColD, a_lo + acol, sw128_desc(w_hi + boff), kIdescBf16, 1u);
+                            mma_ts(tmem + kColD, a_hi + acol, bdesc, kIdescBf16N128, acc0);
+                            mma_ts(tmem + kColD, a_lo + acol, bdesc, kIdescBf16N128, 1u);
+                        } else {
+                            mma_ts(tmem + kColD, a_hi + acol, bdesc, kIdescBf16, acc0);
                         }
                     }
                 }
@@ -488,9 +507,10 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             ci = -sl2e * fmaf(xc, xc, fmaf(xb, xb, xa * xa));
         }
         for (int64_t t = 0; t < tiles; ++t) {
-            const int b = (int)(t & 1);
-            if (t >= 2) {
-                const bool ok = mbar_wait(bar_pempty + 8 * b, (uint32_t)((t - 2) >> 1) & 1, abort_flag, err);
+            const int b = (int)(t % kPBufs);
+            if (t >= kPBufs) {
+                const bool ok = mbar_wait(bar_pempty + 8 * b, (uint32_t)((t - kPBufs) / kPBufs) & 1,
+                                          abort_flag, err);
                 if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
             }
             const int st = (int)(t % kStages);
@@ -499,8 +519,10 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
             tc_fence_after();
-            const float4* yt = reinterpret_cast<const float4*>(smem + SmemLayout::w + st * kStageBytes +
-                                                               kImgBytes) + part * kColsPerWarp;
+            // yhat of this tile, read with explicit shared loads (a generic
+            // pointer here would send every read down the global-load path)
+            const uint32_t yt = sbase + SmemLayout::w + st * kStageBytes + kImgBytes +
+                                part * kColsPerWarp * 16;
             if (TF32) {
                 // 16 columns: one tf32 value per TMEM column; hi keeps the top
                 // 19 bits of p (truncation), lo = p - hi exactly (the MMA then
@@ -508,7 +530,7 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 uint32_t hi[16], lo[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float4 y = yt[q];
+                    const float4 y = lds128(yt + 16 * q);
                     const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
                     const float p = ex2f_tc(e);
                     hi[q] = __float_as_uint(p) & 0xFFFFE000u;
@@ -526,12 +548,23 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                         float p[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const float4 y = yt[c0 + 2 * q + h];
+                            const float4 y = lds128(yt + 16 * (c0 + 2 * q + h));
                             const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
                             p[h] = ex2f_tc(e);
                         }
-                        hi[q] = pack_bf16x2(p[0], p[1]);
-                        lo[q] = pack_bf16x2(p[0] - bf16lo_to_f(hi[q]), p[1] - bf16hi_to_f(hi[q]));
+                        if (SPLIT) {
+                            // hi = top 16 bits of p (truncation, integer ops only:
+                            // the conversion unit is already busy with ex2), lo =
+                            // p - hi exactly, then its top 16 bits: relative
+                            // error <= 2^-16 of p
+                            const uint32_t b0 = __float_as_uint(p[0]), b1 = __float_as_uint(p[1]);
+                            const float r0 = p[0] - __uint_as_float(b0 & 0xFFFF0000u);
+                            const float r1 = p[1] - __uint_as_float(b1 & 0xFFFF0000u);
+                            hi[q] = __byte_perm(b0, b1, 0x7632);
+                            lo[q] = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
+                        } else {
+                            hi[q] = pack_bf16x2(p[0], p[1]);
+                        }
                     }
                     const uint32_t col = kColP + 128 * b + (part * kColsPerWarp + c0) / 2;
                     tmem_st8(lane_base + col, hi);
@@ -555,6 +588,14 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 uint32_t v[16];
                 tmem_ld16(lane_base + kColD + c0, v);
                 tmem_wait_ld();
+                if (SPLIT) {
+                    uint32_t u[16];
+                    tmem_ld16(lane_base + kColD + 64 + c0, u);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(u[q]));
+                }
                 if (row0 + i < m) {
 #pragma unroll
                     for (int q = 0; q < 16; q += 4) {
