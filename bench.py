@@ -483,6 +483,25 @@ def oracle_sample(w, nq, seed=17):
     return int(off[-1]), dt, oracle.num_threads()
 
 
+def probe(spec):
+    """One call per listed item, for ncu captures of a single kernel."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    kind, _, items = spec.partition(":")
+    if kind != "dense":
+        raise SystemExit(f"unknown probe {spec!r}")
+    d = synth.c4()
+    X = torch.from_numpy(synth.pack4(d.X)).cuda()
+    Y = torch.from_numpy(synth.pack4(d.Y)).cuda()
+    W = torch.from_numpy(d.W).cuda()
+    ctx = ab.Context(0)
+    for prec in items.split(","):
+        ab.ab_kernel_matvec(ctx, X, Y, W, d.s, prec)
+    ab.ab_sync(ctx)
+    torch.cuda.synchronize()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,10 +511,16 @@ def main():
     ap.add_argument("--oracle-queries", type=int, default=131072)
     ap.add_argument("--no-also", action="store_true",
                     help="skip the secondary 16.7M-point and dense-operator measurements")
+    ap.add_argument("--probe", default=None,
+                    help="profiling aid: 'dense:bf16x3,tf32x3' runs one full-size dense call "
+                         "per listed precision and exits (no timing, no JSON)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.probe:
+        probe(args.probe)
+        return
 
     if args.impl == "reference":
         if rank != 0:
