@@ -352,6 +352,20 @@ def also_dense(reps=5):
             float((outs[prec].double() - ref).abs().max().item() / scale)
     res["speedup_bf16x3_vs_fp32"] = res["fp32"]["ms"] / res["bf16x3"]["ms"]
     res["speedup_tf32x3_vs_fp32"] = res["fp32"]["ms"] / res["tf32x3"]["ms"]
+    # adjoint: dW, dX, dY and ds (lengthscale) in one call
+    G = torch.from_numpy(d.G).to(dev)
+    dW = torch.empty_like(W)
+    dX = torch.empty_like(X)
+    dY = torch.empty_like(Y)
+    ds = torch.empty((), dtype=torch.float64, device=dev)
+    bwd = {}
+    for prec, reps_b in (("fp32", 1), ("bf16x3", reps), ("tf32x3", reps)):
+        fn = lambda: ab.ab_kernel_matvec_bwd(ctx, X, Y, W, d.s, prec, G, dW, dX, dY, ds)  # noqa: E731
+        fn()
+        bwd[prec] = {"ms": _timed(fn, reps_b, flush)}
+    ab.ab_sync(ctx)
+    bwd["speedup_bf16x3_vs_fp32"] = bwd["fp32"]["ms"] / bwd["bf16x3"]["ms"]
+    res["adjoint_dW_dX_dY_ds"] = bwd
     res["exps"] = m * n
     res["workload"] = "X, Y 65,536 points in [0,1]^3, W 65,536 x 64, Gaussian kernel l = 0.1"
     ctx.close()

@@ -516,7 +516,8 @@ ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, 
     cudaSetDevice(c->device);
     double* partial = nullptr;
     if (ds) {
-        if ((st = ensure_partial(c, (size_t)ab::dense_partial_capacity(m, n))) != AB_OK) return st;
+        // SIMT: one partial per 128-row block; tensor cores: up to two per block
+        if ((st = ensure_partial(c, 2 * (size_t)ab::dense_partial_capacity(m, n) + 2)) != AB_OK) return st;
         partial = c->sc.partial;
     }
     int pc = 0;
@@ -527,18 +528,26 @@ ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, 
     } else {
         if (nrhs != 64)
             return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths need nrhs == 64");
-        // dW = K(Y, X) G on the tensor cores; dX, dY, ds on CUDA cores
-        e = cudaSuccess;
-        if (dW && n > 0) {
-            e = grow(&c->sc.dense_ws, &c->sc.cap_dense_ws, ab::dense_tc_workspace_bytes(m), c->stream);
-            if (e == cudaSuccess)
-                e = ab::launch_dense_tc_fwd(n, m, (const float4*)Y, (const float4*)X, nrhs, G, s, prec,
-                                            dW, c->sc.dense_ws, c->d_err, c->stream);
+        // dW = K(Y, X) G: the forward kernel with the roles swapped;
+        // dX (+ ds) and dY: the tensor-core gradient kernel
+        size_t need = ab::dense_tc_workspace_bytes(m);
+        const size_t g1 = ab::dense_tc_grad_workspace_bytes(m, n);
+        const size_t g2 = ab::dense_tc_grad_workspace_bytes(n, m);
+        if (g1 > need) need = g1;
+        if (g2 > need) need = g2;
+        e = grow(&c->sc.dense_ws, &c->sc.cap_dense_ws, need, c->stream);
+        if (e == cudaSuccess && dW && n > 0)
+            e = ab::launch_dense_tc_fwd(n, m, (const float4*)Y, (const float4*)X, nrhs, G, s, prec, dW,
+                                        c->sc.dense_ws, c->d_err, c->stream);
+        if (e == cudaSuccess && (dX || partial) && m > 0)
+            e = ab::launch_dense_tc_gradx(m, n, (const float4*)X, (const float4*)Y, G, W, s, prec,
+                                          (float4*)dX, partial, &pc, c->sc.dense_ws, c->d_err, c->stream);
+        if (e == cudaSuccess && dY && n > 0) {
+            int pc2 = 0;
+            e = ab::launch_dense_tc_gradx(n, m, (const float4*)Y, (const float4*)X, W, G, s, prec,
+                                          (float4*)dY, nullptr, &pc2, c->sc.dense_ws, c->d_err,
+                                          c->stream);
         }
-        if (e == cudaSuccess)
-            e = ab::launch_dense_bwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s,
-                                     AB_PREC_FP32, G, nullptr, (float4*)dX, (float4*)dY, partial, &pc,
-                                     c->stream);
     }
     if (e == cudaErrorNotSupported)
         return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");

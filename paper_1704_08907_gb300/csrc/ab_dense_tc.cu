@@ -628,6 +628,319 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                      : "memory");
 }
 
+
+// ===========================================================================
+// Adjoint for the rows: dX_i = -2 s sum_j A_ij (x_i - y_j) and
+// ds = -sum_ij A_ij d_ij^2, A_ij = (G_i . W_j) K_ij.
+//
+// S = G W^T on the tensor cores (kind::f16, both operands from shared
+// memory): G and W are split into bf16 hi + lo and S = G_hi W_hi + G_hi W_lo
+// + G_lo W_hi (three products, AB_PREC_*X3) or G_hi W_hi; the accumulator is
+// a 128 x 128 fp32 tile in TMEM, double-buffered.  The epilogue warps read S
+// with tcgen05.ld, recompute K_ij from the centred expanded exponent, and
+// accumulate A (x~_i - y~_j) and A * exponent in registers, so the row sums
+// never cancel.  One CTA per 128 rows; warps 0-15 epilogue (lane quadrant
+// w % 4, 32 of the 128 points of a tile), 16 MMA, 17 producer.  Both the G
+// image of the CTA's rows (once) and the W image + y tile of each Y tile
+// (3-stage ring) arrive by bulk copies.  The same kernel with X <-> Y and
+// G <-> W gives dY.
+// ===========================================================================
+constexpr int kGImg = 2 * 128 * 128;                 // hi + lo blocks, 128 rows x 128 B: 32 KB
+constexpr int kGStage = kGImg + 128 * 16;            // W image + y~ tile: 34 KB
+struct GradSmem {
+    static constexpr int a = 0;                                  // G image (32 KB)
+    static constexpr int ring = kGImg;                            // 3 stages
+    static constexpr int red = ring + kStages * kGStage;          // 4 x 128 x 4 floats
+    static constexpr int bars = red + 4 * 128 * 4 * 4;
+    static constexpr int afull = bars;
+    static constexpr int full = afull + 8;
+    static constexpr int empty = full + 8 * kStages;
+    static constexpr int sfull = empty + 8 * kStages;             // [2]
+    static constexpr int sempty = sfull + 16;                     // [2]
+    static constexpr int done = sempty + 16;
+    static constexpr int tmem_slot = done + 8;
+    static constexpr int abort_flag = tmem_slot + 4;
+    static constexpr int bytes = abort_flag + 4;
+};
+constexpr int kGradSmemBytes = GradSmem::bytes + 1024;
+static_assert(kGImg % 1024 == 0 && kGStage % 1024 == 0, "swizzle alignment");
+
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// [rows x 64] fp32 -> per block of 128 rows: bf16 hi image then lo image,
+// each 128 rows x 128 B, K-major with the 128-byte swizzle.  Rows past
+// `rows` are zero.  One thread per (row, 16-byte chunk).
+__global__ void __launch_bounds__(256)
+k_prep_rows64(int64_t rows, int ncols, const float* __restrict__ src, int64_t blocks,
+              uint8_t* __restrict__ img) {
+    const int64_t total = blocks * 128 * 8;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % 8);
+        const int64_t r = e / 8;
+        const int rb = (int)(r % 128);
+        const int64_t blk = r / 128;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = c * 8 + 2 * q + h;
+                v[h] = (r < rows && col < ncols) ? __ldg(src + r * ncols + col) : 0.0f;
+            }
+            hi[q] = pack_bf16x2(v[0], v[1]);
+            lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
+        }
+        const int64_t off = blk * (int64_t)kGImg + (rb / 8) * 1024 + (rb % 8) * 128 + ((c ^ (rb % 8)) * 16);
+        *reinterpret_cast<uint4*>(img + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(img + off + 16384) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
+// Centred points for the gradient: (y - c, -s' |y - c|^2); padding points
+// get (0, 0, 0, -1e30): their kernel value is 0 and, unlike -inf, the
+// exponent times A = 0 stays 0 in the ds sum.
+__global__ void __launch_bounds__(256)
+k_prep_ytil(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* __restrict__ bbox,
+            float sl2e, float4* __restrict__ Yt, float4* __restrict__ centre) {
+    const float c0 = 0.5f * (ord2f(bbox[0]) + ord2f(bbox[4]));
+    const float c1 = 0.5f * (ord2f(bbox[1]) + ord2f(bbox[5]));
+    const float c2 = 0.5f * (ord2f(bbox[2]) + ord2f(bbox[6]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *centre = make_float4(c0, c1, c2, 0.0f);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (j < n) {
+            const float4 y = __ldg(Y + j);
+            const float a = y.x - c0, b = y.y - c1, c = y.z - c2;
+            Yt[j] = make_float4(a, b, c, -sl2e * fmaf(c, c, fmaf(b, b, a * a)));
+        } else {
+            Yt[j] = make_float4(0.0f, 0.0f, 0.0f, -1e30f);
+        }
+    }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
+                 const float4* __restrict__ Yt, const float4* __restrict__ centre,
+                 const uint8_t* __restrict__ gimg, const uint8_t* __restrict__ wimg, float sl2e,
+                 float s, float4* __restrict__ dX, double* __restrict__ partial,
+                 uint32_t* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar_afull = sbase + GradSmem::afull;
+    const uint32_t bar_full = sbase + GradSmem::full;
+    const uint32_t bar_empty = sbase + GradSmem::empty;
+    const uint32_t bar_sfull = sbase + GradSmem::sfull;
+    const uint32_t bar_sempty = sbase + GradSmem::sempty;
+    const uint32_t bar_done = sbase + GradSmem::done;
+    uint32_t* tmem_slot = (uint32_t*)(smem + GradSmem::tmem_slot);
+    volatile int* abort_flag = (volatile int*)(smem + GradSmem::abort_flag);
+    const int64_t t_begin = total_tiles * blockIdx.y / gridDim.y;
+    const int64_t tiles = total_tiles * (blockIdx.y + 1) / gridDim.y - t_begin;
+    constexpr uint32_t kCols = 256;   // two S buffers of 128 columns
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(bar_afull, 1);
+        for (int q = 0; q < kStages; ++q) {
+            mbar_init(bar_full + 8 * q, 1);
+            mbar_init(bar_empty + 8 * q, 1 + kEpiWarps);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_sfull + 8 * b, 1);
+            mbar_init(bar_sempty + 8 * b, kEpiWarps);
+        }
+        mbar_init(bar_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kEpiWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         sbase + GradSmem::tmem_slot),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t row0 = (int64_t)blockIdx.x * kTM;
+
+    if (warp == kEpiWarps + 1) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar_afull, kGImg);
+            bulk_copy(sbase + GradSmem::a, gimg + blockIdx.x * (int64_t)kGImg, kGImg, bar_afull);
+            int64_t issued = 0;
+            for (int64_t t = 0; t < tiles; ++t) {
+                const int q = (int)(t % kStages);
+                const uint32_t use = (uint32_t)(t / kStages);
+                if (t >= kStages && !mbar_wait(bar_empty + 8 * q, (use - 1) & 1, abort_flag, err)) break;
+                const int64_t gt = t_begin + t;
+                mbar_arrive_expect_tx(bar_full + 8 * q, kGStage);
+                bulk_copy(sbase + GradSmem::ring + q * kGStage, wimg + gt * (int64_t)kGImg, kGImg,
+                          bar_full + 8 * q);
+                bulk_copy(sbase + GradSmem::ring + q * kGStage + kGImg, Yt + gt * 128, 128 * 16,
+                          bar_full + 8 * q);
+                issued = t + 1;
+            }
+            for (int64_t t = issued > kStages ? issued - kStages : 0; t < issued; ++t) {
+                const int q = (int)(t % kStages);
+                const long long t0 = gtimer();
+                while (!mbar_try_wait(bar_full + 8 * q, (uint32_t)(t / kStages) & 1)) {
+                    if (gtimer() - t0 > kWaitLimitNs) {
+                        atomicOr(err, DEVERR_TC_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            const long long t0 = gtimer();
+            while (!mbar_try_wait(bar_afull, 0)) {
+                if (gtimer() - t0 > kWaitLimitNs) {
+                    atomicOr(err, DEVERR_TC_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    } else if (warp == kEpiWarps) {
+        if (lane == 0) {
+            bool ok = mbar_wait(bar_afull, 0, abort_flag, err);
+            for (int64_t t = 0; ok && t < tiles; ++t) {
+                const int q = (int)(t % kStages);
+                const int b = (int)(t & 1);
+                if (!mbar_wait(bar_full + 8 * q, (uint32_t)(t / kStages) & 1, abort_flag, err)) break;
+                if (t >= 2 && !mbar_wait(bar_sempty + 8 * b, (uint32_t)((t - 2) >> 1) & 1, abort_flag, err))
+                    break;
+                tc_fence_after();
+                const uint32_t ga = sbase + GradSmem::a;
+                const uint32_t wb = sbase + GradSmem::ring + q * kGStage;
+                const uint32_t dcol = tmem + 128 * b;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t ahi = sw128_desc(ga + ks * 32), bhi = sw128_desc(wb + ks * 32);
+                    mma_ss(dcol, ahi, bhi, kIdescBf16N128, ks > 0 ? 1u : 0u);
+                    if (SPLIT) {
+                        const uint64_t alo = sw128_desc(ga + 16384 + ks * 32);
+                        const uint64_t blo = sw128_desc(wb + 16384 + ks * 32);
+                        mma_ss(dcol, ahi, blo, kIdescBf16N128, 1u);
+                        mma_ss(dcol, alo, bhi, kIdescBf16N128, 1u);
+                    }
+                }
+                tc_commit(bar_sfull + 8 * b);
+                tc_commit(bar_empty + 8 * q);
+            }
+            // completes once every MMA issued above has finished (also after
+            // an abort); waited for before TMEM is released
+            tc_commit(bar_done);
+        }
+    } else {
+        const int quad = warp & 3, part = warp >> 2;
+        const int i = quad * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        float xt0 = 0.f, xt1 = 0.f, xt2 = 0.f, ci = -1e30f;   // padding row: K = 0
+        if (row0 + i < m) {
+            const float4 x = __ldg(X + row0 + i), c = __ldg(centre);
+            xt0 = x.x - c.x;
+            xt1 = x.y - c.y;
+            xt2 = x.z - c.z;
+            ci = -sl2e * fmaf(xt2, xt2, fmaf(xt1, xt1, xt0 * xt0));
+        }
+        const float xh0 = 2.0f * sl2e * xt0, xh1 = 2.0f * sl2e * xt1, xh2 = 2.0f * sl2e * xt2;
+        float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
+        for (int64_t t = 0; t < tiles; ++t) {
+            const int q = (int)(t % kStages);
+            const int b = (int)(t & 1);
+            bool ok = mbar_wait(bar_sfull + 8 * b, (uint32_t)(t >> 1) & 1, abort_flag, err);
+            ok = ok && mbar_wait(bar_full + 8 * q, (uint32_t)(t / kStages) & 1, abort_flag, err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const uint32_t yt = sbase + GradSmem::ring + q * kGStage + kGImg + part * 32 * 16;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(lane_base + 128 * b + part * 32 + c0, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const float4 y = lds128(yt + 16 * (c0 + k));
+                    const float e = fmaf(xh0, y.x, fmaf(xh1, y.y, fmaf(xh2, y.z, y.w))) + ci;
+                    const float A = __uint_as_float(v[k]) * ex2f_tc(e);
+                    ax = fmaf(A, xt0 - y.x, ax);
+                    ay = fmaf(A, xt1 - y.y, ay);
+                    az = fmaf(A, xt2 - y.z, az);
+                    ae = fmaf(A, e, ae);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(bar_sempty + 8 * b);
+                mbar_arrive(bar_empty + 8 * q);
+            }
+        }
+        // combine the four column slices of each row, then write
+        float* red = (float*)(smem + GradSmem::red);
+        red[(part * 128 + i) * 4 + 0] = ax;
+        red[(part * 128 + i) * 4 + 1] = ay;
+        red[(part * 128 + i) * 4 + 2] = az;
+        red[(part * 128 + i) * 4 + 3] = ae;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const float* red = (const float*)(smem + GradSmem::red);
+        const int i = threadIdx.x;
+        float sx = 0.f, sy = 0.f, sz = 0.f, se = 0.f;
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) {
+            sx += red[(pp * 128 + i) * 4 + 0];
+            sy += red[(pp * 128 + i) * 4 + 1];
+            sz += red[(pp * 128 + i) * 4 + 2];
+            se += red[(pp * 128 + i) * 4 + 3];
+        }
+        if (row0 + i < m && dX && !*abort_flag) {
+            const float4 g = make_float4(-2.0f * s * sx, -2.0f * s * sy, -2.0f * s * sz, 0.0f);
+            if (gridDim.y == 1) dX[row0 + i] = g;
+            else atomicAdd(dX + row0 + i, g);
+        }
+        // ds = -sum A d2 = (1/s') sum A * exponent, exponent = -s' d2
+        double v = (row0 + i < m) ? (double)se / (double)sl2e : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __shared__ double wsum[4];
+        if ((i & 31) == 0) wsum[i >> 5] = v;
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // warps 0-3 only
+        if (i == 0 && partial)
+            partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = wsum[0] + wsum[1] + wsum[2] + wsum[3];
+    }
+    if (warp == kEpiWarps && lane == 0) {
+        const long long t0 = gtimer();
+        while (!mbar_try_wait(bar_done, 0)) {
+            if (gtimer() - t0 > kWaitLimitNs) {
+                atomicOr(err, DEVERR_TC_TIMEOUT);
+                break;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kEpiWarps)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                     : "memory");
+}
+
 }  // namespace
 
 size_t dense_tc_workspace_bytes(int64_t n) {
@@ -677,6 +990,76 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     k_dense_tc_fwd<TF32, SPLIT><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg,
                                                                       sl2e, out, err);
     return cudaGetLastError();
+}
+
+size_t dense_tc_grad_workspace_bytes(int64_t m, int64_t n) {
+    const int64_t mb = (m + 127) / 128, nb = (n + 127) / 128;
+    return (size_t)(mb + nb) * kGImg + (size_t)nb * 128 * 16 + 16 + 32 + 256;
+}
+
+// dX (and ds partials) for rows X against points Y with row weights G and
+// point weights W (both [.][64]); see k_dense_tc_gradx.
+cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* X, const float4* Y,
+                                  const float* G, const float* W, float s, ab_prec prec,
+                                  float4* dX, double* partial, int* partial_count, void* ws,
+                                  uint32_t* err, cudaStream_t st) {
+    *partial_count = 0;
+    if (m <= 0) return cudaSuccess;
+    const int64_t mb = (m + 127) / 128, nb = (n + 127) / 128;
+    cudaError_t e;
+    if (nb == 0) {
+        if (dX) e = cudaMemsetAsync(dX, 0, (size_t)m * sizeof(float4), st);
+        else e = cudaSuccess;
+        return e;
+    }
+    uint8_t* gimg = (uint8_t*)ws;
+    uint8_t* wimg = gimg + (size_t)mb * kGImg;
+    float4* Yt = (float4*)(wimg + (size_t)nb * kGImg);
+    float4* centre = Yt + nb * 128;
+    uint32_t* bbox = (uint32_t*)(centre + 1);
+    k_prep_rows64<<<(unsigned)((mb * 1024 + 255) / 256 < 4096 ? (mb * 1024 + 255) / 256 : 4096), 256, 0,
+                    st>>>(m, kRhs, G, mb, gimg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_prep_rows64<<<(unsigned)((nb * 1024 + 255) / 256 < 4096 ? (nb * 1024 + 255) / 256 : 4096), 256, 0,
+                    st>>>(n, kRhs, W, nb, wimg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bbox, 0xFF, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bbox + 4, 0x00, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const float sl2e = s * kLog2eTC;
+    k_prep_ytil<<<(unsigned)((nb * 128 + 255) / 256), 256, 0, st>>>(n, Y, nb * 128, bbox, sl2e, Yt, centre);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int split = (mb < 4 * (int64_t)g_num_sms && nb >= 2) ? 2 : 1;
+    if (split == 2 && dX && (e = cudaMemsetAsync(dX, 0, (size_t)m * sizeof(float4), st)) != cudaSuccess)
+        return e;
+    const dim3 grid((unsigned)mb, (unsigned)split);
+    if (prec == AB_PREC_BF16 || prec == AB_PREC_TF32) {
+        static bool attr = false;
+        if (!attr) {
+            if ((e = cudaFuncSetAttribute(k_dense_tc_gradx<false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kGradSmemBytes)) != cudaSuccess)
+                return e;
+            attr = true;
+        }
+        k_dense_tc_gradx<false><<<grid, kThreadsTC, kGradSmemBytes, st>>>(m, nb, X, Yt, centre, gimg,
+                                                                          wimg, sl2e, s, dX, partial, err);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            if ((e = cudaFuncSetAttribute(k_dense_tc_gradx<true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kGradSmemBytes)) != cudaSuccess)
+                return e;
+            attr = true;
+        }
+        k_dense_tc_gradx<true><<<grid, kThreadsTC, kGradSmemBytes, st>>>(m, nb, X, Yt, centre, gimg,
+                                                                         wimg, sl2e, s, dX, partial, err);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *partial_count = (int)(mb * split);
+    return cudaSuccess;
 }
 
 cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y, int nrhs,

@@ -132,6 +132,11 @@ AB_HIDDEN size_t dense_tc_workspace_bytes(int64_t n);
 AB_HIDDEN cudaError_t launch_dense_tc_fwd(int64_t m, int64_t n, const float4* X, const float4* Y,
                                           int nrhs, const float* W, float s, ab_prec prec,
                                           float* out, void* ws, uint32_t* err, cudaStream_t st);
+AB_HIDDEN size_t dense_tc_grad_workspace_bytes(int64_t m, int64_t n);
+AB_HIDDEN cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* X, const float4* Y,
+                                            const float* G, const float* W, float s, ab_prec prec,
+                                            float4* dX, double* partial, int* partial_count,
+                                            void* ws, uint32_t* err, cudaStream_t st);
 
 // ab_bd.cu
 AB_HIDDEN cudaError_t launch_bd_step(const Geom& g, int64_t n, float4* pos,

@@ -153,15 +153,38 @@ def test_tensor_core_full_size_sampled_rows(ab, ctx):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
-def test_tensor_core_adjoint_dW(ab, ctx, prec):
-    d = synth.c4(m=3000, n=2000, nrhs=64, seed_offset=5)
-    dW = torch.empty((2000, 64), dtype=torch.float32, device="cuda:0")
-    dX = torch.empty((3000, 4), dtype=torch.float32, device="cuda:0")
+@pytest.mark.parametrize("m,n", [(3000, 2000), (129, 33), (1, 300)])
+def test_tensor_core_adjoint(ab, ctx, prec, m, n):
+    """dW, dX, dY, ds on the tensor-core paths against the FP64 oracle."""
+    d = synth.c4(m=m, n=n, nrhs=64, seed_offset=5 + m)
+    dW = torch.empty((n, 64), dtype=torch.float32, device="cuda:0")
+    dX = torch.empty((m, 4), dtype=torch.float32, device="cuda:0")
+    dY = torch.empty((n, 4), dtype=torch.float32, device="cuda:0")
+    ds = torch.empty((), dtype=torch.float64, device="cuda:0")
     ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, prec, dev(d.G),
-                            dW, dX, None, None)
+                            dW, dX, dY, ds)
     ab.ab_sync(ctx)
     rW = dense.grad_W(d.X, d.Y, d.G, d.s)
     aW = dense.grad_W(d.X, d.Y, np.abs(d.G), d.s)
     assert np.max(np.abs(host(dW) - rW) / aW) <= TC_TOL
     rX = dense.grad_X(d.X, d.Y, d.W, d.G, d.s)
+    rY = dense.grad_Y(d.X, d.Y, d.W, d.G, d.s)
     assert np.max(np.abs(host(dX)[:, :3] - rX)) <= 1e-4 * np.abs(rX).max()
+    assert np.max(np.abs(host(dY)[:, :3] - rY)) <= 1e-4 * np.abs(rY).max()
+    rs = dense.grad_s(d.X, d.Y, d.W, d.G, d.s)
+    As = abs(dense.grad_s(d.X, d.Y, np.abs(d.W), np.abs(d.G), d.s))
+    assert abs(float(ds) - rs) <= TC_TOL * As
+
+
+def test_tensor_core_adjoint_full_size_sampled(ab, ctx):
+    d = synth.c4()
+    m, n = d.X.shape[0], d.Y.shape[0]
+    dX = torch.empty((m, 4), dtype=torch.float32, device="cuda:0")
+    ds = torch.empty((), dtype=torch.float64, device="cuda:0")
+    ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "bf16x3", dev(d.G),
+                            None, dX, None, ds)
+    ab.ab_sync(ctx)
+    rows = synth.query_sample(m, 64, 10)
+    rX = dense.grad_X(d.X, d.Y, d.W, d.G, d.s, rows=rows)
+    assert np.max(np.abs(host(dX)[rows, :3] - rX)) <= 1e-4 * np.abs(rX).max()
+    assert np.isfinite(float(ds))
