@@ -38,6 +38,8 @@ SM_MAX_MHZ = 2070.0
 # Algorithmic FP32 operations: per candidate pair the predicate (3 sub, 3 mul,
 # 2 add, 1 compare); per accepted pair the LJ adjoint term (1 reciprocal,
 # 3 mul for (sig/d)^6, 3 for the coefficient, 2 for (g_i + g_j), 3 FMA).
+# Candidates are those of the paper's method (width-r cells, 3^3 stencil),
+# whatever finer x cells the kernels actually use.
 OPS_PER_CANDIDATE = 9
 OPS_PER_PAIR_LJ_BWD = 12
 OPS_PER_PAIR_LJ_FWD = 7
@@ -121,26 +123,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _stencil_sum_axis(f, axis, periodic):
-    """sum over the distinct stencil neighbours {c-1, c, c+1} along one axis."""
+def _stencil_sum_axis(f, axis, periodic, h=1):
+    """sum over the distinct stencil neighbours c-h .. c+h along one axis."""
     n = f.shape[axis]
     if periodic:
-        if n == 1:
-            return f.copy()
-        if n == 2:
+        if n <= 2 * h:        # every cell of the axis is in every stencil
             return np.broadcast_to(f.sum(axis=axis, keepdims=True), f.shape).copy()
-        return f + np.roll(f, 1, axis=axis) + np.roll(f, -1, axis=axis)
+        out = f.copy()
+        for o in range(1, h + 1):
+            out = out + np.roll(f, o, axis=axis) + np.roll(f, -o, axis=axis)
+        return out
     out = f.copy()
     sl = [slice(None)] * f.ndim
-    if n > 1:
+    for o in range(1, min(h, n - 1) + 1):
         lo_, hi_ = list(sl), list(sl)
-        lo_[axis], hi_[axis] = slice(0, n - 1), slice(1, n)
+        lo_[axis], hi_[axis] = slice(0, n - o), slice(o, n)
         out[tuple(lo_)] += f[tuple(hi_)]
         out[tuple(hi_)] += f[tuple(lo_)]
     return out
 
 
-def candidates_from_cells(start, ncell, periodic, dim):
+def candidates_from_cells(start, ncell, periodic, dim, reach=(1, 1, 1)):
     """Exact candidate count sum_i sum_{c in stencil(cell i)} n_c from the
     cell histogram (measurement only; the stencil is a product of per-axis
     neighbour sets, so the box sum is separable)."""
@@ -148,7 +151,7 @@ def candidates_from_cells(start, ncell, periodic, dim):
     counts = np.diff(start.astype(np.int64)).reshape(shape)
     s = counts
     for k in range(dim):
-        s = _stencil_sum_axis(s, counts.ndim - 1 - k, periodic[k])
+        s = _stencil_sum_axis(s, counts.ndim - 1 - k, periodic[k], reach[k])
     return int((counts * s).sum())
 
 
@@ -190,8 +193,16 @@ def run_ours(args, rank, world):
     ab.ab_build(ctx, dom, pos)
     pairs = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
     perm, start = ab.ab_cell_export(ctx)
-    ncell, _ = ab.ab_cell_shape(ctx)
-    cands = candidates_from_cells(start.cpu().numpy().view(np.uint32), ncell, w.periodic, 3)
+    ncell, _, reach = ab.ab_cell_shape(ctx, with_reach=True)
+    start_h = start.cpu().numpy().view(np.uint32)
+    # candidates the kernels evaluate (x cells split kx ways, reach kx) ...
+    cands_eval = candidates_from_cells(start_h, ncell, w.periodic, 3, reach)
+    # ... and the algorithmic count of the paper's method: width-r cells and
+    # the 3^3 stencil (merge the kx x-parts of every cell back together)
+    kx = reach[0]
+    cnt = np.diff(start_h.astype(np.int64)).reshape(ncell[2], ncell[1], ncell[0] // kx, kx).sum(-1)
+    base_start = np.concatenate([[0], np.cumsum(cnt.ravel())])
+    cands = candidates_from_cells(base_start, (ncell[0] // kx, ncell[1], ncell[2]), w.periodic, 3)
 
     def step(ev=None):
         if ev is not None:
@@ -281,7 +292,8 @@ def run_ours(args, rank, world):
         "config": {"workload": "3-D uniform periodic cube, N=1048576, r=0.0197, "
                                "Lennard-Jones sigma=0.01 eps=1: rebuild + energy + forces",
                    "n": n, "radius": w.radius, "pairs_per_step": pairs,
-                   "candidates_per_step": cands, "l2": "flushed between steps (256 MB write)",
+                   "candidates_per_step": cands, "candidates_evaluated": cands_eval,
+                   "x_cell_split": kx, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,LJ>",
                      "achieved": achieved, "peak": alu_peak, "unit": "Top/s",

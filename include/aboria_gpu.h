@@ -130,7 +130,8 @@ ab_status ab_sync(ab_ctx* ctx);
  *   n_k = max(1, floor(L_k / (r (1 + 2^-18) + L_k 2^-18)))
  * (a width a hair above r, so rounding of the FP32 cell index can never hide
  * a pair from the 3^d stencil), coarsened uniformly if the table would
- * exceed max(2^22, 4n) cells.  Steps: cell hash + histogram, exclusive scan
+ * exceed max(2^22, 4n) cells; then, room permitting, the x cells are split
+ * into kx = 2..4 parts (see ab_cell_shape).  Steps: cell hash + histogram, exclusive scan
  * of the counts (cell offsets), stable counting-sort scatter of the
  * positions.  The sort is stable: within a cell, particles keep ascending
  * original index, so every later result is deterministic.
@@ -143,9 +144,15 @@ ab_status ab_sync(ab_ctx* ctx);
 ab_status ab_build(ab_ctx* ctx, const ab_domain* dom, int64_t n,
                    const float* pos4);
 
-/* Shape of the last cell list: cells per axis (host int32[3]) and the total
- * (host int64).  Errors: AB_ERR_STALE if nothing was built. */
-ab_status ab_cell_shape(ab_ctx* ctx, int32_t* ncell, int64_t* n_cells);
+/* Shape of the last cell list: cells per axis (host int32[3]), the total
+ * (host int64), and the stencil reach per axis (host int32[3]: the box
+ * search visits cells c - reach .. c + reach).  Along x the cells may be a
+ * fraction 1/reach[0] of the cut-off wide (reach[0] in 1..4): a stencil row
+ * then covers (2 reach + 1) / reach cut-off widths instead of 3, with the
+ * same 3^(d-1) rows.  Any pointer may be NULL.  Errors: AB_ERR_STALE if
+ * nothing was built. */
+ab_status ab_cell_shape(ab_ctx* ctx, int32_t* ncell, int64_t* n_cells,
+                        int32_t* reach);
 
 /* Copy out the last cell list for inspection: perm (device uint32[n],
  * perm[s] = original index of sorted slot s) and cell_start (device

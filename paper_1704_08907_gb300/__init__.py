@@ -133,10 +133,14 @@ def ab_build(ctx: Context, dom: _abi.ab_domain, pos4: torch.Tensor):
     return ctx.build_seq
 
 
-def ab_cell_shape(ctx: Context):
+def ab_cell_shape(ctx: Context, with_reach: bool = False):
+    """(cells per axis, total cells[, stencil reach per axis])."""
     nc = (ctypes.c_int32 * 3)()
+    reach = (ctypes.c_int32 * 3)()
     tot = ctypes.c_int64()
-    _check(_lib.ab_cell_shape(ctx.handle, nc, ctypes.byref(tot)), ctx)
+    _check(_lib.ab_cell_shape(ctx.handle, nc, ctypes.byref(tot), reach), ctx)
+    if with_reach:
+        return tuple(nc), tot.value, tuple(reach)
     return tuple(nc), tot.value
 
 

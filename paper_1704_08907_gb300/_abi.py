@@ -52,7 +52,7 @@ SIGNATURES = {
     "ab_set_stream": (ST, [P, P]),
     "ab_sync": (ST, [P]),
     "ab_build": (ST, [P, ctypes.POINTER(ab_domain), I64, P]),
-    "ab_cell_shape": (ST, [P, P, P]),
+    "ab_cell_shape": (ST, [P, P, P, P]),
     "ab_cell_export": (ST, [P, P, P]),
     "ab_pair_sum": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P]),
     "ab_pair_sum_bwd": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P,

@@ -123,14 +123,30 @@ Geom make_geom(const ab_domain* d, int64_t n) {
         for (int k = 0; k < d->dim; ++k) nk[k] = nk[k] > 1 ? nk[k] / 2 : 1;
     }
     g.general = 0;
+    for (int k = 0; k < d->dim; ++k)
+        if (g.periodic[k] && nk[k] < 5) g.general = 1;
+    // Sub-divide x: cells of 1/kx of the width along x, the stencil reaching
+    // kx of them each way.  A stencil row then spans (2 kx + 1) / kx cut-off
+    // widths instead of 3 (fewer candidates) and stays one contiguous range
+    // of the sorted particles.  Needs >= 5 base cells on a periodic x axis
+    // (the fast-path wrap rule then holds with 2 kx + 3 <= kx * n_x) and
+    // room in the cell table.
+    g.kx = 1;
+    if (!g.general && nk[0] >= 5) {
+        const int64_t rest = nk[1] * nk[2];
+        for (int kx = 4; kx >= 2; --kx) {
+            if (nk[0] * kx * rest <= cap && nk[0] * kx <= (int64_t(1) << 21)) {
+                g.kx = kx;
+                nk[0] *= kx;
+                break;
+            }
+        }
+    }
     g.n_cells = 1;
     for (int k = 0; k < 3; ++k) {
         g.n[k] = (int)nk[k];
         g.n_cells *= nk[k];
-        if (k < d->dim) {
-            g.inv_w[k] = (float)((double)nk[k] / (double)g.L[k]);
-            if (g.periodic[k] && nk[k] < 5) g.general = 1;
-        }
+        if (k < d->dim) g.inv_w[k] = (float)((double)nk[k] / (double)g.L[k]);
     }
     return g;
 }
@@ -305,13 +321,18 @@ ab_status ab_build(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos4
     return AB_OK;
 }
 
-ab_status ab_cell_shape(ab_ctx* c, int32_t* ncell, int64_t* n_cells) {
+ab_status ab_cell_shape(ab_ctx* c, int32_t* ncell, int64_t* n_cells, int32_t* reach) {
     if (!c) return AB_ERR_INVALID_ARG;
     ab_status s = require_cells(c);
     if (s != AB_OK) return s;
     if (ncell)
         for (int k = 0; k < 3; ++k) ncell[k] = c->cl.g.n[k];
     if (n_cells) *n_cells = c->cl.g.n_cells;
+    if (reach) {
+        reach[0] = c->cl.g.kx;
+        reach[1] = c->cl.g.dim >= 2 ? 1 : 0;
+        reach[2] = c->cl.g.dim >= 3 ? 1 : 0;
+    }
     return AB_OK;
 }
 

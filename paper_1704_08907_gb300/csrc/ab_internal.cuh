@@ -28,6 +28,7 @@ struct Geom {
     float r2;            // fl(r * r)
     float r;             // radius as given
     int general;         // 1 if a periodic axis has fewer than 5 cells
+    int kx;              // x cells per cut-off width: the stencil spans cx - kx .. cx + kx
     int64_t n_cells;
 };
 

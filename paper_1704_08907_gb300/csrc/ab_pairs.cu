@@ -124,21 +124,24 @@ __device__ __forceinline__ void for_each_segment(const PairParams& P, const floa
     const int cy = cell_coord(pi.y, g.lo[1], g.inv_w[1], g.n[1]);
     const int cz = DIM == 3 ? cell_coord(pi.z, g.lo[2], g.inv_w[2], g.n[2]) : 0;
     const int nx = g.n[0];
-    // x segments: [xa0, xb0] with shift xs0, optional [xa1, xb1] with xs1
+    // x segments: [xa0, xb0] with shift xs0, optional [xa1, xb1] with xs1;
+    // the stencil reaches kx cells each way along x (kx = 1 on the general
+    // path)
+    const int kx = GENERAL ? 1 : g.kx;
     int xa0, xb0, xa1 = 0, xb1 = -1;
     float xs0 = 0.0f, xs1 = 0.0f;
     if (!g.periodic[0]) {
-        xa0 = cx > 0 ? cx - 1 : 0;
-        xb0 = cx < nx - 1 ? cx + 1 : nx - 1;
+        xa0 = cx > kx - 1 ? cx - kx : 0;
+        xb0 = cx < nx - kx ? cx + kx : nx - 1;
     } else if (nx <= 3) {
         xa0 = 0;
         xb0 = nx - 1;
-    } else if (cx == 0) {
-        xa0 = 0; xb0 = 1; xa1 = nx - 1; xb1 = nx - 1; xs1 = GENERAL ? 0.0f : -g.L[0];
-    } else if (cx == nx - 1) {
-        xa0 = nx - 2; xb0 = nx - 1; xa1 = 0; xb1 = 0; xs1 = GENERAL ? 0.0f : g.L[0];
+    } else if (cx - kx < 0) {
+        xa0 = 0; xb0 = cx + kx; xa1 = nx - (kx - cx); xb1 = nx - 1; xs1 = GENERAL ? 0.0f : -g.L[0];
+    } else if (cx + kx >= nx) {
+        xa0 = cx - kx; xb0 = nx - 1; xa1 = 0; xb1 = cx + kx - nx; xs1 = GENERAL ? 0.0f : g.L[0];
     } else {
-        xa0 = cx - 1; xb0 = cx + 1;
+        xa0 = cx - kx; xb0 = cx + kx;
     }
 #pragma unroll 1
     for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {

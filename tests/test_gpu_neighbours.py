@@ -102,6 +102,26 @@ def test_cell_boundary_ulps(ab, ctx):
             _compare_all(ab, ctx, 2, periodic, pos, r)
 
 
+@pytest.mark.parametrize("periodic", [(1, 1), (0, 1)])
+def test_x_subcell_boundary_ulps(ab, ctx, periodic):
+    """Along x the cells are split into kx parts (reach kx): particles one or
+    two ulps either side of every x cell boundary, against brute force."""
+    r = 0.1
+    dom = ab.Domain(2, periodic, r)
+    ab.ab_build(ctx, dom, dev(synth.pack4(np.array([[0.5, 0.5]], np.float32))))
+    (nx, _, _), _, reach = ab.ab_cell_shape(ctx, with_reach=True)
+    assert reach[0] >= 2
+    b = (np.arange(nx + 1) / nx).astype(np.float32)
+    xs = np.concatenate([b, np.nextafter(b, np.float32(-1)), np.nextafter(b, np.float32(2)),
+                         np.nextafter(np.nextafter(b, np.float32(2)), np.float32(2))])
+    xs = np.unique(xs[(xs >= 0) & (xs < 1)]).astype(np.float32)
+    rng = np.random.default_rng(11)
+    ys = rng.choice(np.float32([0.3, 0.3 + 1e-7, 0.35]), len(xs)).astype(np.float32)
+    pos = synth.pack4(np.stack([xs, ys], 1))
+    extra = rng.random((1500, 2)).astype(np.float32)
+    _compare_all(ab, ctx, 2, periodic, np.concatenate([pos, synth.pack4(extra)]), r)
+
+
 def test_degenerate_inputs(ab, ctx):
     # empty
     dom = ab.Domain(3, (1, 1, 1), 0.1)
@@ -139,8 +159,10 @@ def test_sort_is_stable_and_deterministic(ab, ctx):
     seg = np.repeat(np.arange(len(starts) - 1), np.diff(starts))
     same = seg[1:] == seg[:-1]
     assert np.all(perm1[1:][same] > perm1[:-1][same])
-    (nx, ny, nz), tot = ab.ab_cell_shape(ctx)
-    assert (nx, ny, nz) == (50, 50, 50) and tot == 125000
+    (nx, ny, nz), tot, reach = ab.ab_cell_shape(ctx, with_reach=True)
+    kx = reach[0]
+    assert reach[1:] == (1, 1) and 1 <= kx <= 4
+    assert (nx, ny, nz) == (50 * kx, 50, 50) and tot == 125000 * kx
 
 
 def test_c2_full_neighbour_set(ab, ctx):
