@@ -199,10 +199,12 @@ def run_ours(args, rank, world):
     cands_eval = candidates_from_cells(start_h, ncell, w.periodic, 3, reach)
     # ... and the algorithmic count of the paper's method: width-r cells and
     # the 3^3 stencil (merge the kx x-parts of every cell back together)
-    kx = reach[0]
-    cnt = np.diff(start_h.astype(np.int64)).reshape(ncell[2], ncell[1], ncell[0] // kx, kx).sum(-1)
+    kx, ky, kz = reach
+    cnt = np.diff(start_h.astype(np.int64)).reshape(ncell[2] // kz, kz, ncell[1] // ky, ky,
+                                                      ncell[0] // kx, kx).sum(axis=(1, 3, 5))
     base_start = np.concatenate([[0], np.cumsum(cnt.ravel())])
-    cands = candidates_from_cells(base_start, (ncell[0] // kx, ncell[1], ncell[2]), w.periodic, 3)
+    cands = candidates_from_cells(base_start, (ncell[0] // kx, ncell[1] // ky, ncell[2] // kz),
+                                  w.periodic, 3)
 
     def step(ev=None):
         if ev is not None:
@@ -293,7 +295,7 @@ def run_ours(args, rank, world):
                                "Lennard-Jones sigma=0.01 eps=1: rebuild + energy + forces",
                    "n": n, "radius": w.radius, "pairs_per_step": pairs,
                    "candidates_per_step": cands, "candidates_evaluated": cands_eval,
-                   "x_cell_split": kx, "l2": "flushed between steps (256 MB write)",
+                   "cell_split": [kx, ky, kz], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,LJ>",
                      "achieved": achieved, "peak": alu_peak, "unit": "Top/s",

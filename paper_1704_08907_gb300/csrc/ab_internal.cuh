@@ -29,6 +29,7 @@ struct Geom {
     float r;             // radius as given
     int general;         // 1 if a periodic axis has fewer than 5 cells
     int kx;              // x cells per cut-off width: the stencil spans cx - kx .. cx + kx
+    int ky, kz;          // the same for y and z (stencil rows: (2 ky + 1) (2 kz + 1))
     int64_t n_cells;
 };
 

@@ -65,11 +65,12 @@ __device__ __forceinline__ float min_image(float d, float L, float halfL) {
     return d;
 }
 
-// One neighbour coordinate along axis k for offset o in {-1, 0, +1}: returns
+// One neighbour coordinate along axis k for offset o (|o| <= reach): returns
 // false if the offset leaves a non-periodic box or repeats a cell already
-// visited (periodic axes with fewer than 3 cells); *shift receives the
-// fast-path shift (-L when reaching through the lower face, +L through the
-// upper face; only meaningful when every periodic axis has >= 5 cells).
+// visited (periodic axes with fewer than 3 cells, general path only);
+// *shift receives the fast-path shift (-L when reaching through the lower
+// face, +L through the upper face; meaningful when every periodic axis has
+// at least 2 reach + 3 cells).
 __device__ __forceinline__ bool stencil_coord(const Geom& g, int k, int c, int o, int& t,
                                               float& shift) {
     const int n = g.n[k];
@@ -143,13 +144,14 @@ __device__ __forceinline__ void for_each_segment(const PairParams& P, const floa
     } else {
         xa0 = cx - kx; xb0 = cx + kx;
     }
+    const int ky = GENERAL ? 1 : g.ky, kz = GENERAL ? 1 : g.kz;
 #pragma unroll 1
-    for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
+    for (int oz = (DIM == 3 ? -kz : 0); oz <= (DIM == 3 ? kz : 0); ++oz) {
         int z = 0;
         float sz = 0.0f;
         if (DIM == 3 && !stencil_coord(g, 2, cz, oz, z, sz)) continue;
 #pragma unroll 1
-        for (int oy = -1; oy <= 1; ++oy) {
+        for (int oy = -ky; oy <= ky; ++oy) {
             int y;
             float sy;
             if (!stencil_coord(g, 1, cy, oy, y, sy)) continue;

@@ -160,9 +160,9 @@ def test_sort_is_stable_and_deterministic(ab, ctx):
     same = seg[1:] == seg[:-1]
     assert np.all(perm1[1:][same] > perm1[:-1][same])
     (nx, ny, nz), tot, reach = ab.ab_cell_shape(ctx, with_reach=True)
-    kx = reach[0]
-    assert reach[1:] == (1, 1) and 1 <= kx <= 4
-    assert (nx, ny, nz) == (50 * kx, 50, 50) and tot == 125000 * kx
+    kx, ky, kz = reach
+    assert 1 <= kx <= 4 and 1 <= ky <= 2 and kz == 1
+    assert (nx, ny, nz) == (50 * kx, 50 * ky, 50) and tot == 125000 * kx * ky
 
 
 def test_c2_full_neighbour_set(ab, ctx):
