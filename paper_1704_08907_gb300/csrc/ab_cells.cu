@@ -20,8 +20,11 @@ namespace {
 constexpr int kThreads = 256;
 
 inline int ew_grid(int64_t n) {
+    // one thread per element up to 64 blocks per SM: the build kernels are
+    // latency-bound (dependent loads and atomics), so they want many loads in
+    // flight rather than long grid-stride loops
     int64_t b = (n + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)g_num_sms * 8;
+    int64_t cap = (int64_t)g_num_sms * 64;
     if (b > cap) b = cap;
     return b < 1 ? 1 : (int)b;
 }
@@ -205,16 +208,24 @@ k_scan(const uint32_t* in, TOut* out, int64_t n, uint64_t* status,
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_reduce_partials(const double* __restrict__ partial, int count,
-                  double* __restrict__ out) {
-    __shared__ double s[kThreads];
-    double a = 0.0;
-    for (int t = threadIdx.x; t < count; t += kThreads) a += partial[t];
-    s[threadIdx.x] = a;
+constexpr int kRedThreads = 1024;
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_partials(const double* __restrict__ partial, int count, double* __restrict__ out) {
+    // fixed assignment and tree order: deterministic for a given count
+    __shared__ double s[kRedThreads];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int t = threadIdx.x;
+    for (; t + 3 * kRedThreads < count; t += 4 * kRedThreads) {
+        a0 += partial[t];
+        a1 += partial[t + kRedThreads];
+        a2 += partial[t + 2 * kRedThreads];
+        a3 += partial[t + 3 * kRedThreads];
+    }
+    for (; t < count; t += kRedThreads) a0 += partial[t];
+    s[threadIdx.x] = (a0 + a1) + (a2 + a3);
     __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = s[0];
@@ -257,7 +268,7 @@ cudaError_t launch_scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n,
 
 cudaError_t launch_reduce_partials(const double* partial, int count, double* out,
                                    cudaStream_t st) {
-    k_reduce_partials<<<1, kThreads, 0, st>>>(partial, count, out);
+    k_reduce_partials<<<1, kRedThreads, 0, st>>>(partial, count, out);
     return cudaGetLastError();
 }
 
