@@ -234,6 +234,32 @@ __device__ __forceinline__ float ex2f_tc(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic: each half rounds exactly like
+// the scalar FP32 instruction) for the epilogue, which evaluates two columns
+// per instruction.
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 // Two floats -> packed bf16x2 (lo element in the low half), round to nearest.
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     uint32_t r;
@@ -347,6 +373,9 @@ k_bbox(int64_t n, const float4* __restrict__ Y, uint32_t* __restrict__ bbox) {
 // Centring keeps every term below s' * (half-diagonal^2) in magnitude, so the
 // FP32 rounding of the expanded form stays ~1e-5 in the exponent.  Padding
 // points get yhat = (0, 0, 0, -inf): their kernel values are exactly 0.
+// Layout: points in pairs (2p, 2p+1), each pair as two float4
+//   (x0, x1, y0, y1), (z0, z1, w0, w1)
+// so the epilogue loads a column pair's components as packed FP32 pairs.
 __global__ void __launch_bounds__(256)
 k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* __restrict__ bbox,
          float sl2e, float4* __restrict__ Yhat, float4* __restrict__ centre) {
@@ -354,16 +383,23 @@ k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* 
     const float c1 = 0.5f * (ord2f(bbox[1]) + ord2f(bbox[5]));
     const float c2 = 0.5f * (ord2f(bbox[2]) + ord2f(bbox[6]));
     if (blockIdx.x == 0 && threadIdx.x == 0) *centre = make_float4(c0, c1, c2, 0.0f);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        if (j < n) {
-            const float4 y = __ldg(Y + j);
-            const float a = y.x - c0, b = y.y - c1, c = y.z - c2;
-            const float nrm = fmaf(c, c, fmaf(b, b, a * a));
-            Yhat[j] = make_float4(2.0f * sl2e * a, 2.0f * sl2e * b, 2.0f * sl2e * c, -sl2e * nrm);
-        } else {
-            Yhat[j] = make_float4(0.0f, 0.0f, 0.0f, -__int_as_float(0x7f800000));
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 2 * p < npad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float4 h[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t j = 2 * p + u;
+            if (j < n) {
+                const float4 y = __ldg(Y + j);
+                const float a = y.x - c0, b = y.y - c1, c = y.z - c2;
+                const float nrm = fmaf(c, c, fmaf(b, b, a * a));
+                h[u] = make_float4(2.0f * sl2e * a, 2.0f * sl2e * b, 2.0f * sl2e * c, -sl2e * nrm);
+            } else {
+                h[u] = make_float4(0.0f, 0.0f, 0.0f, -__int_as_float(0x7f800000));
+            }
         }
+        Yhat[2 * p] = make_float4(h[0].x, h[1].x, h[0].y, h[1].y);
+        Yhat[2 * p + 1] = make_float4(h[0].z, h[1].z, h[0].w, h[1].w);
     }
 }
 
@@ -506,6 +542,8 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             xc = x.z - c.z;
             ci = -sl2e * fmaf(xc, xc, fmaf(xb, xb, xa * xa));
         }
+        const uint64_t xa2 = f2pack(xa, xa), xb2 = f2pack(xb, xb), xc2 = f2pack(xc, xc);
+        const uint64_t ci2 = f2pack(ci, ci);
         for (int64_t t = 0; t < tiles; ++t) {
             const int b = (int)(t % kPBufs);
             if (t >= kPBufs) {
@@ -523,18 +561,36 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             // pointer here would send every read down the global-load path)
             const uint32_t yt = sbase + SmemLayout::w + st * kStageBytes + kImgBytes +
                                 part * kColsPerWarp * 16;
+            // exponent of a column pair with packed FP32 pairs:
+            //   e = xa yx + (xb yy + (xc yz + (yw + ci)))
+            auto exponent2 = [&](int pair, float& e0, float& e1) {
+                const float4 A = lds128(yt + 32 * pair), B = lds128(yt + 32 * pair + 16);
+                uint64_t e = add2(f2pack(B.z, B.w), ci2);
+                e = fma2(xc2, f2pack(B.x, B.y), e);
+                e = fma2(xb2, f2pack(A.z, A.w), e);
+                e = fma2(xa2, f2pack(A.x, A.y), e);
+                f2unpack(e, e0, e1);
+            };
             if (TF32) {
                 // 16 columns: one tf32 value per TMEM column; hi keeps the top
                 // 19 bits of p (truncation), lo = p - hi exactly (the MMA then
                 // reads lo's top 19 bits: relative error <= 2^-20 of p)
                 uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 y = lds128(yt + 16 * q);
-                    const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
-                    const float p = ex2f_tc(e);
-                    hi[q] = __float_as_uint(p) & 0xFFFFE000u;
-                    lo[q] = __float_as_uint(p - __uint_as_float(hi[q]));
+                for (int q = 0; q < 8; ++q) {
+                    float e0, e1;
+                    exponent2(q, e0, e1);
+                    const float p0 = ex2f_tc(e0), p1 = ex2f_tc(e1);
+                    hi[2 * q] = __float_as_uint(p0) & 0xFFFFE000u;
+                    hi[2 * q + 1] = __float_as_uint(p1) & 0xFFFFE000u;
+                    if (SPLIT) {
+                        float r0, r1;
+                        f2unpack(sub2(f2pack(p0, p1), f2pack(__uint_as_float(hi[2 * q]),
+                                                             __uint_as_float(hi[2 * q + 1]))),
+                                 r0, r1);
+                        lo[2 * q] = __float_as_uint(r0);
+                        lo[2 * q + 1] = __float_as_uint(r1);
+                    }
                 }
                 const uint32_t col = kColP + 128 * b + part * kColsPerWarp;
                 tmem_st16(lane_base + col, hi);
@@ -545,25 +601,23 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                     uint32_t hi[8], lo[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        float p[2];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float4 y = lds128(yt + 16 * (c0 + 2 * q + h));
-                            const float e = fmaf(xa, y.x, fmaf(xb, y.y, fmaf(xc, y.z, y.w))) + ci;
-                            p[h] = ex2f_tc(e);
-                        }
+                        float e0, e1;
+                        exponent2(c0 / 2 + q, e0, e1);
+                        const float p0 = ex2f_tc(e0), p1 = ex2f_tc(e1);
                         if (SPLIT) {
                             // hi = top 16 bits of p (truncation, integer ops only:
                             // the conversion unit is already busy with ex2), lo =
                             // p - hi exactly, then its top 16 bits: relative
                             // error <= 2^-16 of p
-                            const uint32_t b0 = __float_as_uint(p[0]), b1 = __float_as_uint(p[1]);
-                            const float r0 = p[0] - __uint_as_float(b0 & 0xFFFF0000u);
-                            const float r1 = p[1] - __uint_as_float(b1 & 0xFFFF0000u);
+                            const uint32_t b0 = __float_as_uint(p0), b1 = __float_as_uint(p1);
+                            float r0, r1;
+                            f2unpack(sub2(f2pack(p0, p1), f2pack(__uint_as_float(b0 & 0xFFFF0000u),
+                                                                 __uint_as_float(b1 & 0xFFFF0000u))),
+                                     r0, r1);
                             hi[q] = __byte_perm(b0, b1, 0x7632);
                             lo[q] = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
                         } else {
-                            hi[q] = pack_bf16x2(p[0], p[1]);
+                            hi[q] = pack_bf16x2(p0, p1);
                         }
                     }
                     const uint32_t col = kColP + 128 * b + (part * kColsPerWarp + c0) / 2;
@@ -970,7 +1024,7 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const float sl2e = s * kLog2eTC;
-    k_prep_y<<<(unsigned)((tiles * TN + 255) / 256), 256, 0, st>>>(n, Y, tiles * TN, bbox, sl2e, Yhat,
+    k_prep_y<<<(unsigned)((tiles * TN / 2 + 255) / 256), 256, 0, st>>>(n, Y, tiles * TN, bbox, sl2e, Yhat,
                                                                    centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t mblocks = (m + kTM - 1) / kTM;
