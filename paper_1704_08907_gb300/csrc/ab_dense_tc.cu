@@ -596,7 +596,7 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 tmem_st16(lane_base + col, hi);
                 if (SPLIT) tmem_st16(lane_base + col + 64, lo);
             } else {
-#pragma unroll 1
+#pragma unroll
                 for (int c0 = 0; c0 < kColsPerWarp; c0 += 16) {
                     uint32_t hi[8], lo[8];
 #pragma unroll
@@ -610,10 +610,8 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                             // p - hi exactly, then its top 16 bits: relative
                             // error <= 2^-16 of p
                             const uint32_t b0 = __float_as_uint(p0), b1 = __float_as_uint(p1);
-                            float r0, r1;
-                            f2unpack(sub2(f2pack(p0, p1), f2pack(__uint_as_float(b0 & 0xFFFF0000u),
-                                                                 __uint_as_float(b1 & 0xFFFF0000u))),
-                                     r0, r1);
+                            const float r0 = p0 - __uint_as_float(b0 & 0xFFFF0000u);
+                            const float r1 = p1 - __uint_as_float(b1 & 0xFFFF0000u);
                             hi[q] = __byte_perm(b0, b1, 0x7632);
                             lo[q] = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
                         } else {

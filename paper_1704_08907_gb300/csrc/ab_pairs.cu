@@ -40,6 +40,7 @@ struct PairParams {
     int64_t n;
     Geom g;
     float s, s_log2e, eps, sig2, c, k, r;
+    float zero;   // 0.0f, passed at run time (see sq2)
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -164,24 +165,62 @@ __device__ __forceinline__ void for_each_segment(const PairParams& P, const floa
     }
 }
 
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic; each half rounds exactly like
+// the scalar FP32 instruction).  The x and y components of one float4 sit in
+// an aligned register pair, so the predicate forms (dx, dy) and their squares
+// with one instruction each.  Squares are fma(d, d, z) with z a zero known
+// only at run time: rounded once, exactly like fl(d * d), and never
+// contracted further with the following addition.
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sq2(uint64_t a, uint64_t z) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(a), "l"(z));
+    return d;
+}
+
 // Predicate separation (canonical FP32 rule) for candidate pj.
 template <int DIM, bool GENERAL, bool SHIFTED>
 __device__ __forceinline__ float pred_d2(const Geom& g, const float4& pi, const float4& pj,
                                          float sx, float sy, float sz, float& dx, float& dy,
-                                         float& dz) {
-    dx = __fsub_rn(pj.x, pi.x);
-    dy = __fsub_rn(pj.y, pi.y);
-    dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
+                                         float& dz, float zero) {
     if (GENERAL) {
+        dx = __fsub_rn(pj.x, pi.x);
+        dy = __fsub_rn(pj.y, pi.y);
+        dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
         if (g.periodic[0]) dx = min_image(dx, g.L[0], g.halfL[0]);
         if (g.periodic[1]) dy = min_image(dy, g.L[1], g.halfL[1]);
         if (DIM == 3 && g.periodic[2]) dz = min_image(dz, g.L[2], g.halfL[2]);
-    } else if (SHIFTED) {
-        dx = __fadd_rn(dx, sx);
-        dy = __fadd_rn(dy, sy);
+        float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        if (DIM == 3) d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+        return d2;
+    }
+    uint64_t dxy = sub2(f2pack(pj.x, pj.y), f2pack(pi.x, pi.y));
+    dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
+    if (SHIFTED) {
+        dxy = add2(dxy, f2pack(sx, sy));
         if (DIM == 3) dz = __fadd_rn(dz, sz);
     }
-    float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    float qx, qy;
+    f2unpack(sq2(dxy, f2pack(zero, zero)), qx, qy);
+    f2unpack(dxy, dx, dy);
+    float d2 = __fadd_rn(qx, qy);
     if (DIM == 3) d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
     return d2;
 }
@@ -194,15 +233,18 @@ __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
                                             const float4& pi, F&& f) {
     const Geom& g = P.g;
     const float r2 = g.r2;
-    for_each_segment<DIM, GENERAL>(P, pi, [&](uint32_t a, uint32_t b, float sx, float sy,
+    for_each_segment<DIM, GENERAL>(P, pi, [&](uint32_t a0, uint32_t b0, float sx, float sy,
                                               float sz) {
+      // the segment holding the particle itself is walked as [a0, s), (s, b0)
+      uint32_t a = a0, b = (a0 <= s && s < b0) ? s : b0;
+      for (;;) {
         if (GENERAL || sx != 0.0f || sy != 0.0f || sz != 0.0f) {
 #pragma unroll 1
             for (uint32_t j = a; j < b; ++j) {
                 const float4 pj = __ldg(P.spos + j);
                 float dx, dy, dz;
-                const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz);
-                if (d2 < r2 && j != s) {
+                const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz, P.zero);
+                if (d2 < r2) {
                     dx = value_sep(pi.x, pj.x, g.periodic[0], g.L[0], g.halfL[0]);
                     dy = value_sep(pi.y, pj.y, g.periodic[1], g.L[1], g.halfL[1]);
                     if (DIM == 3) dz = value_sep(pi.z, pj.z, g.periodic[2], g.L[2], g.halfL[2]);
@@ -214,10 +256,14 @@ __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
             for (uint32_t j = a; j < b; ++j) {
                 const float4 pj = __ldg(P.spos + j);
                 float dx, dy, dz;
-                const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz);
-                if (d2 < r2 && j != s) f(j, pj, dx, dy, dz, d2);
+                const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz, P.zero);
+                if (d2 < r2) f(j, pj, dx, dy, dz, d2);
             }
         }
+        if (b >= b0) break;
+        a = b + 1;
+        b = b0;
+      }
     });
 }
 
@@ -247,7 +293,7 @@ __device__ __forceinline__ void visit_pairs_batched(const PairParams& P, uint32_
                 for (uint32_t k = 0; k < cnt; ++k) {
                     const float4 pj = __ldg(P.spos + j0 + k);
                     float dx, dy, dz;
-                    const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz);
+                    const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz, P.zero);
                     if (d2 < r2) m |= 1u << k;
                 }
             } else {
@@ -255,7 +301,7 @@ __device__ __forceinline__ void visit_pairs_batched(const PairParams& P, uint32_
                 for (uint32_t k = 0; k < cnt; ++k) {
                     const float4 pj = __ldg(P.spos + j0 + k);
                     float dx, dy, dz;
-                    const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz);
+                    const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz, P.zero);
                     if (d2 < r2) m |= 1u << k;
                 }
             }
@@ -441,6 +487,7 @@ PairParams make_params(const CellList& cl, const ab_op_params& prm, const float2
     P.c = prm.c;
     P.k = prm.k;
     P.r = cl.g.r;
+    P.zero = 0.0f;
     return P;
 }
 
