@@ -226,8 +226,8 @@ __device__ __forceinline__ float pred_d2(const Geom& g, const float4& pi, const 
 }
 
 // Direct visit: f(j, pj, dx, dy, dz, d2) for every accepted pair, with value
-// separations accurate to one rounding (see value_sep).  Used for operators
-// whose per-pair body is a few instructions.
+// separations accurate to one rounding (see value_sep).  Used by every pair
+// kernel.
 template <int DIM, bool GENERAL, class F>
 __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
                                             const float4& pi, F&& f) {
@@ -267,66 +267,6 @@ __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
     });
 }
 
-// Batched visit.  The predicate loop tests up to 32 consecutive candidates
-// of a segment and records acceptances in a per-lane bit mask; the mask is
-// then drained with body(j, pj, dx, dy, dz, d2), positions reloaded (an L1
-// hit) and value separations recomputed.  With ~15% of candidates accepted,
-// evaluating the body inside the predicate loop would make the whole warp pay
-// for a body on nearly every iteration; draining per batch costs the warp
-// max-over-lanes(popcount) bodies per batch instead, and needs no shared
-// memory (so occupancy and L1 capacity for the neighbour loads are kept).
-// The self pair is removed from the mask once per batch, not per candidate.
-template <int DIM, bool GENERAL, class B>
-__device__ __forceinline__ void visit_pairs_batched(const PairParams& P, uint32_t s,
-                                                    const float4& pi, B&& body) {
-    const Geom& g = P.g;
-    const float r2 = g.r2;
-    for_each_segment<DIM, GENERAL>(P, pi, [&](uint32_t a, uint32_t b, float sx, float sy,
-                                              float sz) {
-        const bool shifted = GENERAL || sx != 0.0f || sy != 0.0f || sz != 0.0f;
-#pragma unroll 1
-        for (uint32_t j0 = a; j0 < b; j0 += 32) {
-            const uint32_t cnt = min(b - j0, 32u);
-            uint32_t m = 0;
-            if (shifted) {
-#pragma unroll 1
-                for (uint32_t k = 0; k < cnt; ++k) {
-                    const float4 pj = __ldg(P.spos + j0 + k);
-                    float dx, dy, dz;
-                    const float d2 = pred_d2<DIM, GENERAL, true>(g, pi, pj, sx, sy, sz, dx, dy, dz, P.zero);
-                    if (d2 < r2) m |= 1u << k;
-                }
-            } else {
-#pragma unroll 4
-                for (uint32_t k = 0; k < cnt; ++k) {
-                    const float4 pj = __ldg(P.spos + j0 + k);
-                    float dx, dy, dz;
-                    const float d2 = pred_d2<DIM, false, false>(g, pi, pj, 0.f, 0.f, 0.f, dx, dy, dz, P.zero);
-                    if (d2 < r2) m |= 1u << k;
-                }
-            }
-            if (s - j0 < cnt) m &= ~(1u << (s - j0));
-            while (m) {
-                const uint32_t k = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t j = j0 + k;
-                const float4 pj = __ldg(P.spos + j);
-                float dx, dy, dz;
-                if (shifted) {
-                    dx = value_sep(pi.x, pj.x, g.periodic[0], g.L[0], g.halfL[0]);
-                    dy = value_sep(pi.y, pj.y, g.periodic[1], g.L[1], g.halfL[1]);
-                    dz = DIM == 3 ? value_sep(pi.z, pj.z, g.periodic[2], g.L[2], g.halfL[2]) : 0.0f;
-                } else {
-                    dx = __fsub_rn(pj.x, pi.x);
-                    dy = __fsub_rn(pj.y, pi.y);
-                    dz = DIM == 3 ? __fsub_rn(pj.z, pi.z) : 0.0f;
-                }
-                body(j, pj, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-            }
-        }
-    });
-}
-
 // FP64 block sum of one value per thread into partial[blockIdx.x].
 template <int THREADS>
 __device__ __forceinline__ void block_partial(double v, double* partial) {
@@ -359,8 +299,7 @@ k_pair_fwd(PairParams P, PairOut o) {
     o.out[__ldg(P.perm + s)] = a0;
 }
 
-// Forward for LJ / EXPF / SOFT: direct visit (measured faster than the
-// batched drain for these short bodies).
+// Forward for LJ / EXPF / SOFT: direct visit.
 template <int DIM, bool GENERAL, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd_q(PairParams P, PairOut o) {
@@ -401,7 +340,9 @@ k_pair_fwd_q(PairParams P, PairOut o) {
     if (OP == AB_OP_LJ && o.partial) block_partial<kPairThreads>(live ? (double)a0 : 0.0, o.partial);
 }
 
-// Adjoints (GAUSS, LJ): batched visit.
+// Adjoints (GAUSS, LJ): direct visit.  (A batched variant that collected
+// acceptances in a per-lane bit mask and evaluated the bodies when draining
+// it measured 6-15% slower once the predicate was packed.)
 template <int DIM, bool GENERAL, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_bwd(PairParams P, PairOut o) {
@@ -410,7 +351,7 @@ k_pair_bwd(PairParams P, PairOut o) {
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 vi = live ? __ldg(P.sv + s) : make_float2(0.f, 0.f);
     float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f;
-    if (live) visit_pairs_batched<DIM, GENERAL>(P, s, pi,
+    if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
         [&](uint32_t j, const float4&, float dx, float dy, float dz, float d2) {
             const float2 vj = __ldg(P.sv + j);
             if (OP == AB_OP_GAUSS) {
