@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -422,6 +423,107 @@ def also_c3(reps=5):
             "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True}
 
 
+def also_md(loop_steps=200):
+    """The paper's molecular-dynamics example (Sec. 3): 2-D periodic unit
+    square, exponential force of Eq. 1 with c = 1e-3, semi-implicit Euler with
+    dt = 1 (Eqs. 2-3).  Fig. 3 shapes: N/T_e for r = sqrt(3/N) (left, ~9.4
+    neighbours) and r = sqrt(3/500) (right, neighbours grow with N).  T_e is
+    the velocity update of Eq. 2 as the paper times it: the force sum on the
+    current cell list plus v += f (ab_pair_sum EXPF + ab_md_step, the latter
+    applied to a scratch copy of the positions so that the cell list stays
+    valid).  step = rebuild + force + Eqs. 2-3.  Also a time loop at
+    N = 2^20."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = ab.Context(dev.index)
+    prm = ab.OpParams(c=1.0e-3)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def point(n, r):
+        w = synth.paper_shape(n)
+        pos = torch.from_numpy(w.pos).to(dev)
+        scratch = pos.clone()
+        vel = torch.zeros_like(pos)
+        F = torch.empty_like(pos)
+        dom = ab.Domain(2, (1, 1), r)
+        ab.ab_build(ctx, dom, pos)
+        pairs = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
+        reps = max(5, min(2000, int(2e8 / max(pairs + n, 1))))
+
+        def te():
+            ab.ab_pair_sum(ctx, "expf", prm, out=F)
+            ab.ab_md_step(ctx, dom, scratch, vel, F, 1.0)
+
+        def step():
+            ab.ab_build(ctx, dom, pos)
+            ab.ab_pair_sum(ctx, "expf", prm, out=F)
+            ab.ab_md_step(ctx, dom, pos, vel, F, 1.0)
+
+        te_ms = timed(te, reps)
+        step_ms = timed(step, reps)
+        # the same velocity update replayed from a CUDA graph of 20 updates:
+        # at small N the eager numbers are host launch latency, not GPU time
+        graph_te_ms = None
+        try:
+            ab.ab_build(ctx, dom, pos)
+            te()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream(dev)
+            cap.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(cap):
+                with torch.cuda.graph(g, stream=cap):
+                    for _ in range(20):
+                        te()
+            torch.cuda.current_stream(dev).wait_stream(cap)
+            graph_te_ms = timed(g.replay, max(3, reps // 20)) / 20
+        except Exception:   # capture unavailable: report the eager numbers only
+            graph_te_ms = None
+        return {"N": n, "r": r, "neighbours_mean": pairs / n, "reps": reps,
+                "te_ms": te_ms, "N_over_Te_per_s": n / (te_ms * 1e-3),
+                "te_graph_ms": graph_te_ms,
+                "N_over_Te_graph_per_s": n / (graph_te_ms * 1e-3) if graph_te_ms else None,
+                "step_ms": step_ms, "N_over_Tstep_per_s": n / (step_ms * 1e-3)}
+
+    left = [point(1 << k, math.sqrt(3.0 / (1 << k))) for k in range(4, 25, 2)]
+    right = [point(1 << k, math.sqrt(3.0 / 500.0)) for k in range(4, 18, 2)]
+    # the time loop: N = 2^20, rebuild + force + step every step
+    n = 1 << 20
+    w = synth.paper_shape(n)
+    pos = torch.from_numpy(w.pos).to(dev)
+    vel = torch.zeros_like(pos)
+    F = torch.empty_like(pos)
+    dom = ab.Domain(2, (1, 1), w.radius)
+
+    def loop_step():
+        ab.ab_build(ctx, dom, pos)
+        ab.ab_pair_sum(ctx, "expf", prm, out=F)
+        ab.ab_md_step(ctx, dom, pos, vel, F, 1.0)
+
+    ms = timed(loop_step, loop_steps)
+    ab.ab_sync(ctx)
+    vsum = vel[:, :2].double().sum(dim=0).abs().max().item()
+    return {"workload": "paper Sec. 3 example: 2-D periodic, EXPF c=1e-3, semi-implicit Euler dt=1",
+            "fig3_left_r_sqrt3_over_N": left, "fig3_right_r_sqrt3_over_500": right,
+            "time_loop_N1048576": {"steps": loop_steps + 3, "ms_per_step": ms,
+                                   "particle_steps_per_s": n / (ms * 1e-3),
+                                   "total_momentum_abs_max": vsum},
+            "gpu_launches_per_step": 7}
+
+
 def also_bd(steps=100):
     """2-D Brownian dynamics, 4,194,304 particles, x periodic / y reflecting,
     soft repulsion within r = 0.002, Euler-Maruyama dt = 1e-5 with Philox
@@ -583,7 +685,7 @@ def main():
     out, w = run_ours(args, rank, world)
     if rank == 0 and not args.no_also and world == 1:
         out["also"] = {"c3_clustered_16M": also_c3(), "dense_kernel_matvec": also_dense(),
-                       "brownian_4M_2d": also_bd()}
+                       "brownian_4M_2d": also_bd(), "paper_md_example": also_md()}
     if rank == 0:
         pairs, secs, cores = oracle_sample(w, args.oracle_queries)
         out["cpu_baseline"] = {"value": pairs / secs, "unit": UNIT, "cores": cores,

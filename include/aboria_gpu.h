@@ -250,6 +250,25 @@ ab_status ab_bd_step(ab_ctx* ctx, const ab_domain* dom, int64_t n,
                      float* pos4, const float* force4, float dt, float D,
                      uint64_t seed, uint64_t step);
 
+/* One step of the semi-implicit (symplectic) Euler integrator of the paper's
+ * molecular-dynamics example (Sec. 3, Eqs. 2-3), with step dt (the paper
+ * uses dt = 1 and folds the constant c into the force):
+ *   v_i <- v_i + dt a_i,   x_i <- x_i + dt v_i   (the updated v_i),
+ * a_i being for example the EXPF pair sum of ab_pair_sum (Eq. 1).
+ *   dom:   the domain; periodic axes wrap into [lo, hi) (a value that rounds
+ *          to hi becomes lo); on a non-periodic axis a particle that leaves
+ *          [lo, hi] is reflected once at the wall and that component of its
+ *          velocity reversed.
+ *   pos4, vel4: device float32[n][4], updated in place (x, y, z; the fourth
+ *          component and unused axes are left unchanged).
+ *   acc4:  device float32[n][4], read only.
+ * Arithmetic: FP32, each product and sum rounded separately (no FMA).
+ * If pos4 is the array of the last ab_build, the cell list is marked stale.
+ * Errors: AB_ERR_INVALID_ARG (NULL or unaligned arrays, non-finite dt,
+ * bad domain), AB_ERR_ALIAS (any two arrays overlap), AB_ERR_CUDA. */
+ab_status ab_md_step(ab_ctx* ctx, const ab_domain* dom, int64_t n,
+                     float* pos4, float* vel4, const float* acc4, float dt);
+
 /* Allocation-free exclusive prefix sum of n uint32 values (the paper has no
  * counterpart: this is a service for callers that cannot allocate device
  * memory).  out[k] = in[0] + ... + in[k-1] for 0 <= k < n, wrapping modulo

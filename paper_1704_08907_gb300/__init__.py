@@ -237,6 +237,15 @@ def ab_bd_step(ctx: Context, dom, pos4, force4, dt, D, seed, step):
                            _ptr(force4), float(dt), float(D), int(seed), int(step)), ctx)
 
 
+def ab_md_step(ctx: Context, dom, pos4, vel4, acc4, dt=1.0):
+    """Semi-implicit Euler step (Sec. 3, Eqs. 2-3): v += dt a, x += dt v."""
+    for t, nm in [(pos4, "pos4"), (vel4, "vel4"), (acc4, "acc4")]:
+        _dev(t, torch.float32, (4,), nm)
+    ctx._stream()
+    _check(_lib.ab_md_step(ctx.handle, ctypes.byref(dom), pos4.shape[0], _ptr(pos4), _ptr(vel4),
+                           _ptr(acc4), float(dt)), ctx)
+
+
 def ab_testing_scan_timeout(ctx: Context, items: int, skip_tile: int, limit_ns: int):
     ctx._stream()
     _check(_lib.ab_testing_scan_timeout(ctx.handle, int(items), int(skip_tile),

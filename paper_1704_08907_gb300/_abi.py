@@ -62,6 +62,7 @@ SIGNATURES = {
     "ab_kernel_matvec_bwd": (ST, [P, I64, I64, P, P, I32, P, F32, ctypes.c_int, P,
                                   P, P, P, P]),
     "ab_bd_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, F32, F32, U64, U64]),
+    "ab_md_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, P, F32]),
     "ab_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ab_last_error": (ctypes.c_char_p, [P]),
     "ab_testing_scan_timeout": (ST, [P, I64, I32, I64]),

@@ -604,6 +604,27 @@ ab_status ab_bd_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4,
     return AB_OK;
 }
 
+ab_status ab_md_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4, float* vel4,
+                     const float* acc4, float dt) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = check_domain(c, dom);
+    if (s != AB_OK) return s;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(c, AB_ERR_INVALID_ARG, "n out of range");
+    if (n > 0 && (!pos4 || !vel4 || !acc4 || !aligned16(pos4) || !aligned16(vel4) || !aligned16(acc4)))
+        return fail(c, AB_ERR_INVALID_ARG, "pos4/vel4/acc4 must be non-NULL and 16-byte aligned");
+    if (!isfinite(dt)) return fail(c, AB_ERR_INVALID_ARG, "dt must be finite");
+    const size_t b = (size_t)n * 16;
+    if (overlaps(pos4, b, vel4, b) || overlaps(pos4, b, acc4, b) || overlaps(vel4, b, acc4, b))
+        return fail(c, AB_ERR_ALIAS, "pos4, vel4 and acc4 must not overlap");
+    cudaSetDevice(c->device);
+    Geom g = make_geom(dom, 0);
+    cudaError_t e = ab::launch_md_step(g, n, (float4*)pos4, (float4*)vel4, (const float4*)acc4, dt,
+                                       c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_md_step");
+    if (pos4 == c->cl.user_pos) c->cl.valid = false;
+    return AB_OK;
+}
+
 // ---- testing hooks -------------------------------------------------------
 
 ab_status ab_testing_scan_timeout(ab_ctx* c, int64_t items, int32_t skip_tile,

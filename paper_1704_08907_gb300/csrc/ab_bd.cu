@@ -11,6 +11,13 @@
 // Periodic axes wrap into [lo, hi); non-periodic axes reflect once.
 // Element-wise and HBM-bound: one float4 read, one float4 force read, one
 // float4 write per particle.
+//
+// Also here: the semi-implicit (symplectic) Euler step of the paper's worked
+// molecular-dynamics example (Sec. 3, Eqs. 2-3), generalised to a step dt:
+//   v_i <- v_i + dt a_i,   x_i <- x_i + dt v_i  (the new velocity),
+// with a_i the summed pair force (the EXPF pair sum of Eq. 1, or any other).
+// Periodic axes wrap as above; at a wall of a non-periodic axis the position
+// is reflected once and that velocity component reversed.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -107,12 +114,43 @@ k_bd_step(int64_t n, float4* __restrict__ pos, const float4* __restrict__ force,
     }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(256)
+k_md_step(int64_t n, float4* __restrict__ pos, float4* __restrict__ vel,
+          const float4* __restrict__ acc, StepGeom g, float dt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 p = pos[i], v = vel[i];
+        const float4 a = __ldg(acc + i);
+        float pp[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z};
+        const float aa[3] = {a.x, a.y, a.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k >= g.dim) break;
+            float vk = __fadd_rn(vv[k], __fmul_rn(dt, aa[k]));   // Eq. 2
+            float y = __fadd_rn(pp[k], __fmul_rn(dt, vk));        // Eq. 3
+            if (g.periodic[k]) {
+                const float t = floorf(__fdiv_rn(y - g.lo[k], g.L[k]));
+                y = y - t * g.L[k];
+                if (y >= g.hi[k] || y < g.lo[k]) y = g.lo[k];
+            } else {
+                if (y < g.lo[k]) {
+                    y = 2.0f * g.lo[k] - y;
+                    vk = -vk;
+                }
+                if (y > g.hi[k]) {
+                    y = 2.0f * g.hi[k] - y;
+                    vk = -vk;
+                }
+            }
+            pp[k] = y;
+            vv[k] = vk;
+        }
+        pos[i] = make_float4(pp[0], pp[1], pp[2], p.w);
+        vel[i] = make_float4(vv[0], vv[1], vv[2], v.w);
+    }
+}
 
-cudaError_t launch_bd_step(const Geom& geo, int64_t n, float4* pos, const float4* force,
-                           float dt, float D, uint64_t seed, uint64_t step,
-                           cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+StepGeom step_geom(const Geom& geo) {
     StepGeom g;
     g.dim = geo.dim;
     for (int k = 0; k < 3; ++k) {
@@ -121,6 +159,26 @@ cudaError_t launch_bd_step(const Geom& geo, int64_t n, float4* pos, const float4
         g.L[k] = geo.L[k];
         g.hi[k] = geo.lo[k] + geo.L[k];
     }
+    return g;
+}
+
+}  // namespace
+
+cudaError_t launch_md_step(const Geom& geo, int64_t n, float4* pos, float4* vel,
+                           const float4* acc, float dt, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)g_num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_md_step<<<(unsigned)blocks, 256, 0, st>>>(n, pos, vel, acc, step_geom(geo), dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bd_step(const Geom& geo, int64_t n, float4* pos, const float4* force,
+                           float dt, float D, uint64_t seed, uint64_t step,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const StepGeom g = step_geom(geo);
     const float amp = (float)sqrt(2.0 * (double)D * (double)dt);
     int64_t blocks = (n + 255) / 256;
     const int64_t cap = (int64_t)g_num_sms * 8;

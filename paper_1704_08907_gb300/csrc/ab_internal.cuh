@@ -145,5 +145,7 @@ AB_HIDDEN cudaError_t launch_bd_step(const Geom& g, int64_t n, float4* pos,
                                      const float4* force, float dt, float D,
                                      uint64_t seed, uint64_t step,
                                      cudaStream_t st);
+AB_HIDDEN cudaError_t launch_md_step(const Geom& g, int64_t n, float4* pos, float4* vel,
+                                     const float4* acc, float dt, cudaStream_t st);
 
 }  // namespace ab
