@@ -524,6 +524,43 @@ def also_md(loop_steps=200):
             "gpu_launches_per_step": 7}
 
 
+def also_solve():
+    """Kernel-system solve (K(X, X) + sigma^2 I) W = B by conjugate gradients
+    on the dense operator (RBF interpolation with a nugget / GP posterior
+    mean, Sec. 1.1): X = the 65,536 dense-workload points, 64 right-hand
+    sides ~ N(0, 1), Gaussian kernel l = 0.1, sigma^2 = 1, tol = 1e-4.  The
+    true residual is checked on 64 sampled rows against the oracle's FP64
+    matvec."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    from oracle import dense as odense
+    d = synth.c4()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X = torch.from_numpy(synth.pack4(d.X)).to(dev)
+    Bh = np.random.default_rng(1704089 + 40).standard_normal((d.X.shape[0], 64)).astype(np.float32)
+    B = torch.from_numpy(Bh).to(dev)
+    ctx = ab.Context(dev.index)
+    sigma2, tol = 1.0, 1e-4
+    rows = synth.query_sample(d.X.shape[0], 64, 41)
+    res = {"workload": "n=65,536 points in [0,1]^3, 64 rhs, Gaussian l=0.1 (s=50), sigma^2=1, "
+                       "CG tol=1e-4 from W=0", "tol": tol, "sigma2": sigma2}
+    for prec in ("bf16x3", "fp32"):
+        ab.ab_kernel_solve(ctx, X, B, d.s, sigma2, prec, tol, 3)    # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W, it, rr = ab.ab_kernel_solve(ctx, X, B, d.s, sigma2, prec, tol, 2000)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        Wh = W.cpu().numpy().astype(np.float64)
+        ax = odense.matvec(d.X[rows], d.X, Wh, d.s) + sigma2 * Wh[rows]
+        sampled = float(np.abs(Bh[rows] - ax).max() / np.sqrt((Bh.astype(np.float64) ** 2).mean()))
+        res[prec] = {"iterations": it, "seconds": secs, "ms_per_iteration": secs * 1e3 / max(it, 1),
+                     "relative_residual": rr, "sampled_rows_residual_over_rms_b": sampled}
+    res["speedup_bf16x3_vs_fp32"] = res["fp32"]["seconds"] / res["bf16x3"]["seconds"]
+    ab.ab_sync(ctx)
+    return res
+
+
 def also_bd(steps=100):
     """2-D Brownian dynamics, 4,194,304 particles, x periodic / y reflecting,
     soft repulsion within r = 0.002, Euler-Maruyama dt = 1e-5 with Philox
@@ -685,7 +722,8 @@ def main():
     out, w = run_ours(args, rank, world)
     if rank == 0 and not args.no_also and world == 1:
         out["also"] = {"c3_clustered_16M": also_c3(), "dense_kernel_matvec": also_dense(),
-                       "brownian_4M_2d": also_bd(), "paper_md_example": also_md()}
+                       "brownian_4M_2d": also_bd(), "paper_md_example": also_md(),
+                       "kernel_solve_cg": also_solve()}
     if rank == 0:
         pairs, secs, cores = oracle_sample(w, args.oracle_queries)
         out["cpu_baseline"] = {"value": pairs / secs, "unit": UNIT, "cores": cores,

@@ -250,6 +250,31 @@ ab_status ab_bd_step(ab_ctx* ctx, const ab_domain* dom, int64_t n,
                      float* pos4, const float* force4, float dt, float D,
                      uint64_t seed, uint64_t step);
 
+/* Solve (K(X, X) + sigma2 I) W = B for W, K_ij = exp(-s |x_i - x_j|^2): the
+ * linear system of RBF interpolation with a nugget and of the Gaussian-
+ * process posterior mean (paper Sec. 1.1; Rasmussen and Williams, Ch. 2).
+ * Conjugate gradients (Hestenes and Stiefel), one independent iteration per
+ * right-hand side, from W = 0; each iteration is one ab_kernel_matvec of the
+ * chosen precision plus per-column FP64 inner products reduced in a fixed
+ * order (run-to-run deterministic).  A column stops when
+ * ||r|| <= tol ||b|| (r the recurrence residual); the call returns when all
+ * have stopped or after max_iter iterations.
+ *   n, X:   points, device float32[n][4] (16-byte aligned).
+ *   nrhs, B: device float32[n][nrhs] right-hand sides; nrhs <= 64, and
+ *           exactly 64 for the tensor-core precisions.
+ *   s:      kernel scale; sigma2: the nugget sigma^2 >= 0 (sigma2 > 0 keeps
+ *           the system well conditioned).
+ *   W:      device float32[n][nrhs], the solution (overwritten).
+ *   iters, relres: optional host outputs, the iterations run and the largest
+ *           ||r||/||b|| over the columns.
+ * Synchronises the context's stream once per iteration (the stopping test).
+ * Errors: AB_ERR_INVALID_ARG, AB_ERR_ALIAS (W overlaps X or B),
+ * AB_ERR_UNSUPPORTED, AB_ERR_OOM, AB_ERR_CUDA. */
+ab_status ab_kernel_solve(ab_ctx* ctx, int64_t n, const float* X, int32_t nrhs,
+                          const float* B, float s, float sigma2, ab_prec prec,
+                          float tol, int32_t max_iter, float* W, int32_t* iters,
+                          float* relres);
+
 /* One step of the semi-implicit (symplectic) Euler integrator of the paper's
  * molecular-dynamics example (Sec. 3, Eqs. 2-3), with step dt (the paper
  * uses dt = 1 and folds the constant c into the force):

@@ -229,6 +229,26 @@ def ab_kernel_matvec_bwd(ctx: Context, X, Y, W, s, prec, G, dW=None, dX=None, dY
     return dW, dX, dY, ds
 
 
+def ab_kernel_solve(ctx: Context, X, B, s, sigma2, prec="fp32", tol=1e-5, max_iter=1000,
+                    W=None):
+    """Solve (K(X, X) + sigma2 I) W = B by conjugate gradients (Sec. 1.1).
+    Returns (W, iterations, largest relative residual)."""
+    prec = PRECS.get(prec, prec)
+    _dev(X, torch.float32, (4,), "X")
+    _dev(B, torch.float32, None, "B")
+    n, nrhs = X.shape[0], B.shape[1]
+    if W is None:
+        W = torch.empty((n, nrhs), dtype=torch.float32, device=ctx.device)
+    _dev(W, torch.float32, None, "W")
+    it = ctypes.c_int32()
+    rr = ctypes.c_float()
+    ctx._stream()
+    _check(_lib.ab_kernel_solve(ctx.handle, n, _ptr(X), nrhs, _ptr(B), float(s), float(sigma2),
+                                prec, float(tol), int(max_iter), _ptr(W), ctypes.byref(it),
+                                ctypes.byref(rr)), ctx)
+    return W, it.value, rr.value
+
+
 def ab_bd_step(ctx: Context, dom, pos4, force4, dt, D, seed, step):
     _dev(pos4, torch.float32, (4,), "pos4")
     _dev(force4, torch.float32, (4,), "force4")

@@ -63,6 +63,8 @@ SIGNATURES = {
                                   P, P, P, P]),
     "ab_bd_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, F32, F32, U64, U64]),
     "ab_md_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, P, F32]),
+    "ab_kernel_solve": (ST, [P, I64, P, I32, P, F32, F32, I32, F32, I32, P,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "ab_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ab_last_error": (ctypes.c_char_p, [P]),
     "ab_testing_scan_timeout": (ST, [P, I64, I32, I64]),

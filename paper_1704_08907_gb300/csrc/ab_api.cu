@@ -240,7 +240,7 @@ ab_status ab_destroy(ab_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_id, c->cl.rank, c->cl.tmp,
                     c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
-                    c->sc.partial, c->sc.counts, c->sc.dense_ws};
+                    c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -513,6 +513,47 @@ ab_status ab_kernel_matvec(ab_ctx* c, int64_t m, int64_t n, const float* X, cons
     if (e == cudaErrorNotSupported)
         return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");
     return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "ab_kernel_matvec");
+}
+
+ab_status ab_kernel_solve(ab_ctx* c, int64_t n, const float* X, int32_t nrhs, const float* B,
+                          float s, float sigma2, ab_prec prec, float tol, int32_t max_iter, float* W,
+                          int32_t* iters, float* relres) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status st = check_dense(c, n, n, X, X, nrhs, B, prec);
+    if (st != AB_OK) return st;
+    if (n > 0 && !W) return fail(c, AB_ERR_INVALID_ARG, "W is NULL");
+    if (!isfinite(s) || !isfinite(sigma2) || sigma2 < 0.0f || !(tol > 0.0f) || !isfinite(tol) ||
+        max_iter < 0)
+        return fail(c, AB_ERR_INVALID_ARG, "need finite s, sigma2 >= 0, tol > 0, max_iter >= 0");
+    if (prec != AB_PREC_FP32 && nrhs != 64)
+        return fail(c, AB_ERR_UNSUPPORTED, "tensor-core paths need nrhs == 64");
+    const size_t vb = (size_t)n * nrhs * 4;
+    if (overlaps(W, vb, X, (size_t)n * 16) || overlaps(W, vb, B, vb))
+        return fail(c, AB_ERR_ALIAS, "W overlaps an input");
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0f;
+    if (n == 0) return AB_OK;
+    cudaSetDevice(c->device);
+    cudaError_t e = grow(&c->sc.solve_ws, &c->sc.cap_solve_ws, ab::solve_workspace_bytes(n, nrhs),
+                         c->stream);
+    if (e == cudaSuccess && prec != AB_PREC_FP32)
+        e = grow(&c->sc.dense_ws, &c->sc.cap_dense_ws, ab::dense_tc_workspace_bytes(n), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_solve workspace");
+    const float4* X4 = (const float4*)X;
+    const ab::SolveMatvec mv = [&](const float* P, float* Q) -> cudaError_t {
+        if (prec == AB_PREC_FP32) return ab::launch_dense_fwd(n, n, X4, X4, nrhs, P, s, prec, Q, c->stream);
+        return ab::launch_dense_tc_fwd(n, n, X4, X4, nrhs, P, s, prec, Q, c->sc.dense_ws, c->d_err,
+                                       c->stream);
+    };
+    int it = 0;
+    float rr = 0.0f;
+    e = ab::run_solve(n, nrhs, B, sigma2, tol, max_iter, W, c->sc.solve_ws, mv, &it, &rr, c->stream);
+    if (e == cudaErrorNotSupported)
+        return fail(c, AB_ERR_UNSUPPORTED, "precision not available for this shape");
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_kernel_solve");
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return AB_OK;
 }
 
 ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, const float* Y,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "../../include/aboria_gpu.h"
 
 #define AB_HIDDEN __attribute__((visibility("hidden")))
@@ -70,6 +72,8 @@ struct Scratch {
     size_t cap_counts = 0;
     uint8_t* dense_ws = nullptr;      // tensor-core operand images
     size_t cap_dense_ws = 0;
+    uint8_t* solve_ws = nullptr;      // CG vectors and scalars
+    size_t cap_solve_ws = 0;
 };
 
 // ---- launchers (defined in the .cu files) ----------------------------------
@@ -139,6 +143,14 @@ AB_HIDDEN cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* 
                                             const float* G, const float* W, float s, ab_prec prec,
                                             float4* dX, double* partial, int* partial_count,
                                             void* ws, uint32_t* err, cudaStream_t st);
+
+// ab_solve.cu: conjugate gradients for (K(X, X) + sigma^2 I) W = B; the
+// matvec Q = K(X, X) P is supplied by the caller
+using SolveMatvec = std::function<cudaError_t(const float* P, float* Q)>;
+AB_HIDDEN size_t solve_workspace_bytes(int64_t n, int nrhs);
+AB_HIDDEN cudaError_t run_solve(int64_t n, int nrhs, const float* B, float sigma2, float tol,
+                                int max_iter, float* W, void* ws, const SolveMatvec& mv,
+                                int* iters, float* relres, cudaStream_t st);
 
 // ab_bd.cu
 AB_HIDDEN cudaError_t launch_bd_step(const Geom& g, int64_t n, float4* pos,
