@@ -82,7 +82,8 @@ def num_threads() -> int:
     return int(_load().or_num_threads())
 
 
-OPS = {"count": 0, "gauss": 1, "lj": 2, "expf": 3, "soft": 4}
+OPS = {"count": 0, "gauss": 1, "lj": 2, "expf": 3, "soft": 4, "sph_density": 5,
+       "sph_force": 6}
 
 
 def _ptr(a):
@@ -196,8 +197,10 @@ def _eval(op, absmode, box, pos64, offsets, idx, queries, w, params):
     n = pos64.shape[0]
     q = _queries(n, queries)
     w64 = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
-    if OPS[op] == 1 and w64 is None:
-        raise ValueError("gauss needs weights")
+    if OPS[op] in (1, 5, 6) and w64 is None:
+        raise ValueError(f"{op} needs per-particle values w")
+    if OPS[op] == 6 and (w64.ndim != 2 or w64.shape[1] != 2):
+        raise ValueError("sph_force needs w = (m, P/rho^2) as float[n, 2]")
     out = np.zeros((len(q), 4), dtype=np.float64)
     prm = _params(params, box.radius)
     lib.or_pair_eval(OPS[op], absmode, _ptr(prm), box.dim, _ptr(box.periodic),

@@ -306,6 +306,12 @@ void or_cells_list(const or_cells *cl, int64_t nq, const int64_t *queries,
 /*              unshifted; total energy = sum_i y_i)                        */
 /* op 3 EXPF  : y_i = c sum_{j, d>0} -exp(-d) dx_ij / d      (Eq. 1)        */
 /* op 4 SOFT  : y_i = sum_{j, d>0} -k (r - d) dx_ij / d                      */
+/* op 5 SPH_DENSITY: rho_i = m_i W(0) + sum_j m_j W(d), w = m (float64[n]);  */
+/*              Wendland C2 with support r: W(d) = a (1-q)^4 (1+4q), q=d/r, */
+/*              a = 21/(2 pi r^3) (3-D), 7/(pi r^2) (2-D)                   */
+/* op 6 SPH_FORCE: a_i = -sum_j m_j (A_i + A_j) grad_i W(d_ij),              */
+/*              w = (m, A) per particle (float64[n][2], A = P/rho^2);       */
+/*              grad_i W = W'(d) (x_i - x_j)/d, W'(d) = -20 a q (1-q)^3 / r  */
 /*                                                                          */
 /* pos64: float64[n][4]; w: float64[n] (GAUSS) or NULL; out: float64[nq][4] */
 /* (scalar ops write out[q][0]).  prm = {s, eps, sigma, c, k, r}.           */
@@ -331,6 +337,8 @@ void or_pair_eval(int op, int absmode, const double *prm, int dim,
     box_init(&b, dim, periodic, lo, hi, (float)prm[5]);
     const double s = prm[0], eps = prm[1], sig = prm[2], c = prm[3],
                  kk = prm[4], r = prm[5];
+    const double pi_ = 3.14159265358979323846;
+    const double wend_a = dim == 3 ? 21.0 / (2.0 * pi_ * r * r * r) : 7.0 / (pi_ * r * r);
     (void)n;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t q = 0; q < nq; ++q) {
@@ -363,9 +371,21 @@ void or_pair_eval(int op, int absmode, const double *prm, int dim,
                     if (absmode && op == 4) mag = kk * (r + d);
                     for (int k = 0; k < dim; ++k) t[k] = mag * dx[k] / d;
                 }
+            } else if (op == 5) {
+                const double q1 = sqrt(d2) / r, u = 1.0 - q1;
+                t[0] = w[j] * wend_a * u * u * u * u * (1.0 + 4.0 * q1);
+            } else if (op == 6) {
+                /* a_i = sum_j m_j (A_i + A_j) W'(d)/d dx_ij, W'(d)/d = -20 a (1-q)^3 / r^2;
+                 * the metric counts |A_i| + |A_j| */
+                const double q1 = sqrt(d2) / r, u = 1.0 - q1;
+                const double aa = absmode ? fabs(w[2 * i + 1]) + fabs(w[2 * j + 1])
+                                          : w[2 * i + 1] + w[2 * j + 1];
+                const double coef = w[2 * j] * aa * (-20.0 * wend_a * u * u * u / (r * r));
+                for (int k = 0; k < dim; ++k) t[k] = coef * dx[k];
             }
             for (int k = 0; k < 3; ++k) acc[k] += absmode ? fabs(t[k]) : t[k];
         }
+        if (op == 5) acc[0] += (absmode ? fabs(w[i]) : w[i]) * wend_a;   /* the particle itself */
         for (int k = 0; k < 4; ++k) out[4 * q + k] = acc[k];
     }
 }
