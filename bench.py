@@ -561,6 +561,51 @@ def also_solve():
     return res
 
 
+def also_sph(steps=50):
+    """SPH density + symmetric pressure force (Wendland C2, support r) on
+    1,048,576 uniform points in the periodic unit cube, r for ~57 neighbours
+    (a typical SPH support), masses 1/N.  One step = rebuild + density +
+    force; the per-particle P/rho^2 input of the force comes from the
+    equation of state P = rho - 1 evaluated once before timing."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    n = 1 << 20
+    r = (57.0 / (4.0 / 3.0 * math.pi * n)) ** (1.0 / 3.0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pos = torch.from_numpy(synth.uniform_positions(n, 3, 1704089 + 50)).to(dev)
+    m = torch.full((n,), 1.0 / n, dtype=torch.float32, device=dev)
+    ctx = ab.Context(dev.index)
+    dom = ab.Domain(3, (1, 1, 1), r)
+    ab.ab_build(ctx, dom, pos)
+    pairs = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
+    rho = ab.ab_pair_sum(ctx, "sph_density", ab.OpParams(), w=m)
+    wv = torch.stack([m, (rho - 1.0) / (rho * rho)], 1).contiguous()
+    F = torch.empty((n, 4), dtype=torch.float32, device=dev)
+
+    def step():
+        ab.ab_build(ctx, dom, pos)
+        ab.ab_pair_sum(ctx, "sph_density", ab.OpParams(), w=m, out=rho)
+        ab.ab_pair_sum(ctx, "sph_force", ab.OpParams(), w=wv, out=F)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ab.ab_sync(ctx)
+    return {"workload": "SPH, N=1,048,576 uniform periodic cube, Wendland C2 support r=%.5f "
+                        "(~57 neighbours): rebuild + density + pressure force" % r,
+            "steps": steps, "ms_per_step": ms, "pairs_per_step": pairs,
+            "pair_evaluations_per_s": 2 * pairs / (ms * 1e-3),
+            "mean_density": float(rho.double().mean().item())}
+
+
 def also_bd(steps=100):
     """2-D Brownian dynamics, 4,194,304 particles, x periodic / y reflecting,
     soft repulsion within r = 0.002, Euler-Maruyama dt = 1e-5 with Philox
@@ -723,7 +768,7 @@ def main():
     if rank == 0 and not args.no_also and world == 1:
         out["also"] = {"c3_clustered_16M": also_c3(), "dense_kernel_matvec": also_dense(),
                        "brownian_4M_2d": also_bd(), "paper_md_example": also_md(),
-                       "kernel_solve_cg": also_solve()}
+                       "kernel_solve_cg": also_solve(), "sph_3d_1M": also_sph()}
     if rank == 0:
         pairs, secs, cores = oracle_sample(w, args.oracle_queries)
         out["cpu_baseline"] = {"value": pairs / secs, "unit": UNIT, "cores": cores,

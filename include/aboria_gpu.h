@@ -87,7 +87,13 @@ typedef enum {
     AB_OP_GAUSS = 1,
     AB_OP_LJ = 2,
     AB_OP_EXPF = 3,
-    AB_OP_SOFT = 4
+    AB_OP_SOFT = 4,
+    /* SPH (Sec. 1 lists SPH among the particle methods), Wendland C2 kernel
+     * with support r: W(d) = a (1 - d/r)^4 (1 + 4 d/r),
+     * a = 21 / (2 pi r^3) in 3-D, 7 / (pi r^2) in 2-D (normalised). */
+    AB_OP_SPH_DENSITY = 5,   /* rho_i = m_i W(0) + sum_j m_j W(d_ij); w = m */
+    AB_OP_SPH_FORCE = 6      /* a_i = -sum_j m_j (A_i + A_j) grad_i W(d_ij),
+                                w = (m, A = P / rho^2) per particle */
 } ab_op;
 
 typedef struct {
@@ -171,8 +177,11 @@ ab_status ab_cell_export(ab_ctx* ctx, uint32_t* perm, uint32_t* cell_start);
  *   pair iff d2 < fl(r*r).
  * Values are accumulated in FP32.
  *   op, prm: operator and its parameters (host pointer).
- *   w:       float32[n] weights (GAUSS), else ignored (may be NULL).
- *   out:     float32[n] (COUNT/GAUSS/LJ) or float32[n][4] (EXPF/SOFT).
+ *   w:       float32[n] weights (GAUSS), masses m (SPH_DENSITY), or
+ *            float32[n][2] pairs (m, P/rho^2) (SPH_FORCE); else ignored
+ *            (may be NULL).
+ *   out:     float32[n] (COUNT/GAUSS/LJ/SPH_DENSITY) or float32[n][4]
+ *            (EXPF/SOFT/SPH_FORCE).
  *   energy:  optional device float64[1]; for LJ receives sum_i y_i
  *            (reduced in FP64 in a fixed order), else left unchanged.
  * Errors: AB_ERR_STALE (no build, or positions moved by ab_bd_step since),

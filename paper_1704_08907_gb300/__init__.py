@@ -17,13 +17,14 @@ import torch
 
 from . import _abi
 from ._abi import (AB_OP_COUNT, AB_OP_EXPF, AB_OP_GAUSS, AB_OP_LJ,  # noqa: F401
-                   AB_OP_SOFT, AB_PREC_BF16, AB_PREC_BF16X3, AB_PREC_FP32,
+                   AB_OP_SOFT, AB_OP_SPH_DENSITY, AB_OP_SPH_FORCE, AB_PREC_BF16, AB_PREC_BF16X3, AB_PREC_FP32,
                    AB_PREC_TF32, AB_PREC_TF32X3)
 
 _lib = _abi.load()
 
 OPS = {"count": AB_OP_COUNT, "gauss": AB_OP_GAUSS, "lj": AB_OP_LJ,
-       "expf": AB_OP_EXPF, "soft": AB_OP_SOFT}
+       "expf": AB_OP_EXPF, "soft": AB_OP_SOFT, "sph_density": AB_OP_SPH_DENSITY,
+       "sph_force": AB_OP_SPH_FORCE}
 PRECS = {"fp32": AB_PREC_FP32, "tf32x3": AB_PREC_TF32X3, "bf16x3": AB_PREC_BF16X3,
          "tf32": AB_PREC_TF32, "bf16": AB_PREC_BF16}
 
@@ -157,7 +158,7 @@ def ab_cell_export(ctx: Context):
 def ab_pair_sum(ctx: Context, op, params, w=None, out=None, energy=None):
     """Pair sum over the last cell list; returns ``out`` (allocated if None)."""
     op = OPS.get(op, op)
-    vec = op in (AB_OP_EXPF, AB_OP_SOFT)
+    vec = op in (AB_OP_EXPF, AB_OP_SOFT, AB_OP_SPH_FORCE)
     if out is None:
         shape = (ctx.n, 4) if vec else (ctx.n,)
         out = torch.empty(shape, dtype=torch.float32, device=ctx.device)

@@ -22,7 +22,7 @@ AB_ERR_TIMEOUT = 6
 AB_ERR_UNSUPPORTED = 7
 AB_ERR_CAPACITY = 8
 
-AB_OP_COUNT, AB_OP_GAUSS, AB_OP_LJ, AB_OP_EXPF, AB_OP_SOFT = range(5)
+AB_OP_COUNT, AB_OP_GAUSS, AB_OP_LJ, AB_OP_EXPF, AB_OP_SOFT, AB_OP_SPH_DENSITY, AB_OP_SPH_FORCE = range(7)
 AB_PREC_FP32, AB_PREC_TF32X3, AB_PREC_BF16X3, AB_PREC_TF32, AB_PREC_BF16 = range(5)
 
 # Every function the headers declare, with its ctypes signature.

@@ -182,7 +182,8 @@ ab_status require_cells(ab_ctx* c) {
 }
 
 size_t out_bytes(ab_op op, int64_t n) {
-    return (op == AB_OP_EXPF || op == AB_OP_SOFT) ? (size_t)n * 16 : (size_t)n * 4;
+    return (op == AB_OP_EXPF || op == AB_OP_SOFT || op == AB_OP_SPH_FORCE) ? (size_t)n * 16
+                                                                          : (size_t)n * 4;
 }
 
 }  // namespace
@@ -357,25 +358,31 @@ ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float*
     if (!c) return AB_ERR_INVALID_ARG;
     ab_status s = require_cells(c);
     if (s != AB_OK) return s;
-    if ((int)op < AB_OP_COUNT || (int)op > AB_OP_SOFT) return fail(c, AB_ERR_INVALID_ARG, "unknown op");
+    if ((int)op < AB_OP_COUNT || (int)op > AB_OP_SPH_FORCE)
+        return fail(c, AB_ERR_INVALID_ARG, "unknown op");
     if (!prm) return fail(c, AB_ERR_INVALID_ARG, "params is NULL");
     const int64_t n = c->cl.n;
-    const bool vec = (op == AB_OP_EXPF || op == AB_OP_SOFT);
+    const bool vec = (op == AB_OP_EXPF || op == AB_OP_SOFT || op == AB_OP_SPH_FORCE);
+    const bool uses_w = (op == AB_OP_GAUSS || op == AB_OP_SPH_DENSITY || op == AB_OP_SPH_FORCE);
+    const size_t wb = (size_t)n * (op == AB_OP_SPH_FORCE ? 8 : 4);
     if (n > 0 && !out) return fail(c, AB_ERR_INVALID_ARG, "out is NULL");
     if (vec && !aligned16(out)) return fail(c, AB_ERR_INVALID_ARG, "vector output must be 16-byte aligned");
-    if (op == AB_OP_GAUSS && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "GAUSS needs weights w");
+    if (uses_w && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "this operator needs w");
+    if (op == AB_OP_SPH_FORCE && n > 0 && ((uintptr_t)w & 7u))
+        return fail(c, AB_ERR_INVALID_ARG, "SPH_FORCE w (float32[n][2]) must be 8-byte aligned");
     const size_t ob = out_bytes(op, n);
     // the positions were copied at build time; the inputs here are w only
-    if ((op == AB_OP_GAUSS && overlaps(out, ob, w, (size_t)n * 4)) ||
-        (op == AB_OP_GAUSS && overlaps(energy, 8, w, (size_t)n * 4)) ||
+    if ((uses_w && overlaps(out, ob, w, wb)) || (uses_w && overlaps(energy, 8, w, wb)) ||
         overlaps(energy, 8, out, ob))
         return fail(c, AB_ERR_ALIAS, "output overlaps an input");
     cudaSetDevice(c->device);
     cudaError_t e;
-    if (op == AB_OP_GAUSS) {
+    if (uses_w) {
         if ((s = ensure_sv(c, n)) != AB_OK) return s;
-        if ((e = ab::launch_gather_vars(c->cl, w, nullptr, c->sc.sv, c->stream)) != cudaSuccess)
-            return cuda_fail(c, e, "ab_pair_sum gather");
+        e = op == AB_OP_SPH_FORCE
+                ? ab::launch_gather_pairs(c->cl, (const float2*)w, c->sc.sv, c->stream)
+                : ab::launch_gather_vars(c->cl, w, nullptr, c->sc.sv, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum gather");
     }
     ab::PairOut o;
     o.out = vec ? nullptr : out;

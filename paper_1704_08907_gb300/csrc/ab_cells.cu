@@ -100,6 +100,14 @@ k_gather_vars(int64_t n, const uint32_t* __restrict__ perm,
     }
 }
 
+__global__ void __launch_bounds__(kThreads)
+k_gather_pairs(int64_t n, const uint32_t* __restrict__ perm, const float2* __restrict__ wv,
+               float2* __restrict__ sv) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        sv[s] = __ldg(wv + perm[s]);
+}
+
 // ---------------------------------------------------------------------------
 // (a2) single-pass exclusive scan with decoupled look-back
 // (Merrill & Garland, "Single-pass parallel prefix scan with decoupled
@@ -305,6 +313,13 @@ cudaError_t launch_gather_vars(const CellList& cl, const float* w, const float* 
                                float2* sv, cudaStream_t st) {
     if (cl.n <= 0) return cudaSuccess;
     k_gather_vars<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, w, g, sv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pairs(const CellList& cl, const float2* wv, float2* sv,
+                                cudaStream_t st) {
+    if (cl.n <= 0) return cudaSuccess;
+    k_gather_pairs<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, wv, sv);
     return cudaGetLastError();
 }
 

@@ -84,6 +84,9 @@ AB_HIDDEN cudaError_t launch_build(CellList& cl, const float4* pos, Scratch& sc,
 AB_HIDDEN cudaError_t launch_gather_vars(const CellList& cl, const float* w,
                                          const float* g, float2* sv,
                                          cudaStream_t st);
+// sv[s] = wv[perm[s]]: a per-particle pair of values into sorted order
+AB_HIDDEN cudaError_t launch_gather_pairs(const CellList& cl, const float2* wv, float2* sv,
+                                          cudaStream_t st);
 // Exclusive scan of n u32 counts into out (u32 or u64), out[n] = total.
 // status/ticket: scratch of scan_tiles(n) words + 1 ticket (zeroed here).
 AB_HIDDEN size_t scan_tiles(int64_t n);

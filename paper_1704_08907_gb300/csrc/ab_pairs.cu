@@ -41,7 +41,11 @@ struct PairParams {
     Geom g;
     float s, s_log2e, eps, sig2, c, k, r;
     float zero;   // 0.0f, passed at run time (see sq2)
+    float wend_a;         // Wendland C2 normalisation a (SPH)
+    float inv_r;          // 1 / r
+    float wend_grad;      // -20 a / r^2: W'(d)/d = wend_grad (1 - d/r)^3
 };
+
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -57,6 +61,12 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+// Wendland C2 with support r: t = 1 - d/r (and q = d/r) for a pair at d^2.
+__device__ __forceinline__ float wend_t(float d2, float inv_r, float& q) {
+    const float d = d2 > 0.0f ? d2 * rsqrt_approx(d2) : 0.0f;
+    q = d * inv_r;
+    return fmaxf(1.0f - q, 0.0f);
 }
 
 // Canonical FP32 minimum image along one periodic axis.
@@ -293,9 +303,18 @@ k_pair_fwd(PairParams P, PairOut o) {
     float a0 = 0.0f;
     visit_pairs<DIM, GENERAL>(P, s, pi,
         [&](uint32_t j, const float4&, float, float, float, float d2) {
-            if (OP == AB_OP_COUNT) a0 += 1.0f;
-            else a0 += __ldg(&P.sv[j].x) * ex2_approx(-P.s_log2e * d2);
+            if (OP == AB_OP_COUNT) {
+                a0 += 1.0f;
+            } else if (OP == AB_OP_GAUSS) {
+                a0 += __ldg(&P.sv[j].x) * ex2_approx(-P.s_log2e * d2);
+            } else {   // SPH_DENSITY: m_j W(d)
+                float q;
+                const float t = wend_t(d2, P.inv_r, q);
+                const float t2 = t * t;
+                a0 = fmaf(__ldg(&P.sv[j].x) * P.wend_a, t2 * t2 * fmaf(4.0f, q, 1.0f), a0);
+            }
         });
+    if (OP == AB_OP_SPH_DENSITY) a0 = fmaf(__ldg(&P.sv[s].x), P.wend_a, a0);   // the particle itself
     o.out[__ldg(P.perm + s)] = a0;
 }
 
@@ -307,9 +326,19 @@ k_pair_fwd_q(PairParams P, PairOut o) {
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    const float ai = (OP == AB_OP_SPH_FORCE && live) ? __ldg(&P.sv[s].y) : 0.0f;
     if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
-        [&](uint32_t, const float4&, float dx, float dy, float dz, float d2) {
-            if (OP == AB_OP_LJ) {
+        [&](uint32_t j, const float4&, float dx, float dy, float dz, float d2) {
+            if (OP == AB_OP_SPH_FORCE) {
+                // m_j (A_i + A_j) W'(d)/d dx, W'(d)/d = wend_grad t^3
+                const float2 vj = __ldg(P.sv + j);
+                float q;
+                const float t = wend_t(d2, P.inv_r, q);
+                const float coef = vj.x * (ai + vj.y) * (P.wend_grad * (t * t * t));
+                a0 = fmaf(coef, dx, a0);
+                a1 = fmaf(coef, dy, a1);
+                a2 = fmaf(coef, dz, a2);
+            } else if (OP == AB_OP_LJ) {
                 const float sr2 = P.sig2 * rcp_approx(d2);
                 const float sr6 = sr2 * sr2 * sr2;
                 a0 = fmaf(sr6, sr6 - 1.0f, a0);
@@ -429,6 +458,11 @@ PairParams make_params(const CellList& cl, const ab_op_params& prm, const float2
     P.k = prm.k;
     P.r = cl.g.r;
     P.zero = 0.0f;
+    const double r = (double)cl.g.r, pi = 3.14159265358979323846;
+    const double a = cl.g.dim == 3 ? 21.0 / (2.0 * pi * r * r * r) : 7.0 / (pi * r * r);
+    P.wend_a = (float)a;
+    P.inv_r = (float)(1.0 / r);
+    P.wend_grad = (float)(-20.0 * a / (r * r));
     return P;
 }
 
@@ -460,6 +494,12 @@ cudaError_t launch_pair_fwd(const CellList& cl, ab_op op, const ab_op_params& pr
         case AB_OP_LJ: AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_LJ), P, o); break;
         case AB_OP_EXPF: AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_EXPF), P, o); break;
         case AB_OP_SOFT: AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_SOFT), P, o); break;
+        case AB_OP_SPH_DENSITY:
+            AB_DISPATCH_DG(k_pair_fwd, kPairThreads, COMMA_OP(AB_OP_SPH_DENSITY), P, o);
+            break;
+        case AB_OP_SPH_FORCE:
+            AB_DISPATCH_DG(k_pair_fwd_q, kPairThreads, COMMA_OP(AB_OP_SPH_FORCE), P, o);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
