@@ -44,11 +44,14 @@ SM_MAX_MHZ = 2070.0
 OPS_PER_CANDIDATE = 9
 OPS_PER_PAIR_LJ_BWD = 12
 OPS_PER_PAIR_LJ_FWD = 7
-# DRAM traffic of one k_pair_bwd<3,false,LJ> launch on this workload, from an
-# ncu --set full capture (dram__bytes_read.sum + dram__bytes_write.sum:
-# 32.32 MB + 0.95 MB), valid only for the kernel source it was taken on.
-TRAFFIC_BWD_BYTES = 33.29e6
-TRAFFIC_SOURCE_SHA = "98176c6241ae10c3"
+# energy and gradient together: rcp, sig^2/d^2, its cube, the energy term (2),
+# the force coefficient (3) and three accumulations
+OPS_PER_PAIR_LJ_EG = 12
+# DRAM traffic of one k_pair_lj_eg<3,false> launch on this workload, from an
+# ncu --set full capture (dram__bytes_read.sum + dram__bytes_write.sum), valid
+# only for the kernel source it was taken on (None until captured).
+TRAFFIC_EG_BYTES = 35.40e6   # 29.20 MB read + 6.20 MB written
+TRAFFIC_SOURCE_SHA = "348fe635d7ce98e9"
 
 
 def peaks():
@@ -207,18 +210,26 @@ def run_ours(args, rank, world):
     cands = candidates_from_cells(base_start, (ncell[0] // kx, ncell[1] // ky, ncell[2] // kz),
                                   w.periodic, 3)
 
+    # one step: rebuild + LJ energy and its gradient (the forces) in one walk
     def step(ev=None):
         if ev is not None:
             ev[0].record()
         ab.ab_build(ctx, dom, pos)
         if ev is not None:
             ev[1].record()
-        ab.ab_pair_sum(ctx, "lj", prm, out=E, energy=etot)
+        ab.ab_pair_energy_grad(ctx, "lj", prm, E=E, grad_pos4=F, energy=etot)
         if ev is not None:
             ev[2].record()
+
+    # the same outputs from the separate forward and adjoint kernels
+    def step_unfused(ev):
+        ev[0].record()
+        ab.ab_build(ctx, dom, pos)
+        ev[1].record()
+        ab.ab_pair_sum(ctx, "lj", prm, out=E, energy=etot)
+        ev[2].record()
         ab.ab_pair_sum_bwd(ctx, "lj", prm, None, ones, grad_pos4=F)
-        if ev is not None:
-            ev[3].record()
+        ev[3].record()
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -230,7 +241,7 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
@@ -240,9 +251,22 @@ def run_ours(args, rank, world):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     t_build = np.array([a[0].elapsed_time(a[1]) for a in evs])
-    t_fwd = np.array([a[1].elapsed_time(a[2]) for a in evs])
-    t_bwd = np.array([a[2].elapsed_time(a[3]) for a in evs])
-    t_step = t_build + t_fwd + t_bwd                       # ms, device time
+    t_eg = np.array([a[1].elapsed_time(a[2]) for a in evs])
+    t_step = t_build + t_eg                                # ms, device time
+    # unfused reference: the separate forward and adjoint on the same input
+    ku = min(args.steps, 200)
+    evu = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(ku)]
+    for _ in range(3):
+        step_unfused(evu[0])
+    torch.cuda.synchronize()
+    for k in range(ku):
+        flush.zero_()
+        step_unfused(evu[k])
+    torch.cuda.synchronize()
+    u_build = np.array([a[0].elapsed_time(a[1]) for a in evu])
+    u_fwd = np.array([a[1].elapsed_time(a[2]) for a in evu])
+    u_bwd = np.array([a[2].elapsed_time(a[3]) for a in evu])
+    u_step = float(np.mean(u_build + u_fwd + u_bwd))
     total_ms = float(t_step.sum())
     if world > 1:
         total_ms, value = aggregate_ranks(pairs, total_ms, args.steps, dist, dev)
@@ -257,7 +281,7 @@ def run_ours(args, rank, world):
 
     def e2e_step():
         pos_d.copy_(pos_h, non_blocking=True)
-        ab.lj_energy_forces(ctx, dom, pos_d, eps, sigma, E=E, F=F, energy=etot, g=ones)
+        ab.lj_energy_forces(ctx, dom, pos_d, eps, sigma, E=E, F=F, energy=etot)
         F_h.copy_(F, non_blocking=True)
         e_h.copy_(etot, non_blocking=True)
 
@@ -281,10 +305,11 @@ def run_ours(args, rank, world):
     same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC_SOURCE_SHA
     pk, pk_kind = peaks()
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
-    bwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_BWD
-    bwd_s = float(np.mean(t_bwd)) * 1e-3
-    achieved = bwd_ops / bwd_s / 1e12
+    eg_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_EG
+    eg_s = float(np.mean(t_eg)) * 1e-3
+    achieved = eg_ops / eg_s / 1e12
     fwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_FWD
+    bwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_BWD
     build_bytes = n * (16 + 4 + 4) + n * (4 + 4 + 4 + 4) + n * (4 + 4 + 4 + 16 + 4 + 16) \
         + 8 * (int(np.prod(ncell)) + 1)
     out = {
@@ -298,22 +323,28 @@ def run_ours(args, rank, world):
                    "candidates_per_step": cands, "candidates_evaluated": cands_eval,
                    "cell_split": [kx, ky, kz], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,LJ>",
+        "roofline": {"bound": "alu", "kernel": "k_pair_lj_eg<3,false>",
                      "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                      "frac": achieved / alu_peak,
-                     "traffic": TRAFFIC_BWD_BYTES if same_kernel else None,
-                     "algorithmic_ops_per_launch": bwd_ops,
+                     "traffic": TRAFFIC_EG_BYTES if same_kernel else None,
+                     "algorithmic_ops_per_launch": eg_ops,
                      "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"},
-        "phases_ms": {"build": float(np.mean(t_build)), "fwd": float(np.mean(t_fwd)),
-                      "bwd": float(np.mean(t_bwd))},
+        "phases_ms": {"build": float(np.mean(t_build)), "energy_and_forces": float(np.mean(t_eg))},
         "phase_roofline": {
             "build_hbm_gbs": build_bytes / (float(np.mean(t_build)) * 1e-3) / 1e9,
             "build_hbm_frac": build_bytes / (float(np.mean(t_build)) * 1e-3) / 1e9 / pk["hbm_gbs"],
-            "fwd_alu_frac": fwd_ops / (float(np.mean(t_fwd)) * 1e-3) / 1e12 / alu_peak,
             "peak_kind": pk_kind},
+        "unfused": {
+            "note": "the same outputs from the separate forward (energy) and adjoint "
+                    "(forces, upstream gradient 1) kernels",
+            "steps": ku, "ms_per_step": u_step, "value": pairs / (u_step * 1e-3),
+            "phases_ms": {"build": float(np.mean(u_build)), "fwd": float(np.mean(u_fwd)),
+                          "bwd": float(np.mean(u_bwd))},
+            "fwd_alu_frac": fwd_ops / (float(np.mean(u_fwd)) * 1e-3) / 1e12 / alu_peak,
+            "bwd_alu_frac": bwd_ops / (float(np.mean(u_bwd)) * 1e-3) / 1e12 / alu_peak},
         "e2e": {"value": pairs * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16 + 8},
-        "gpu_launches": 8 * args.steps,
+        "gpu_launches": 6 * args.steps,
         "wall_s": wall,
     }
     if clk:
@@ -415,12 +446,28 @@ def also_c3(reps=5):
     for _ in range(2):
         step()
     ms = _timed(step, reps)
+    # phase split of the same step (CUDA events between the three calls)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ph = np.zeros(3)
+    for _ in range(reps):
+        ev[0].record()
+        ab.ab_build(ctx, dom, pos)
+        ev[1].record()
+        ab.ab_pair_sum(ctx, "gauss", prm, w=wt, out=y)
+        ev[2].record()
+        ab.ab_pair_sum_bwd(ctx, "gauss", prm, wt, g, gpos, gw, gs)
+        ev[3].record()
+        torch.cuda.synchronize()
+        ph += [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
+    (nx, ny, nz), ncells, reach = ab.ab_cell_shape(ctx, with_reach=True)
     ab.ab_sync(ctx)
     ctx.close()
     return {"workload": "16,777,216 points in 1024 Gaussian blobs, periodic cube, "
                         f"r={w.radius:.7f} (64 neighbours mean): rebuild + gauss fwd + adjoint",
             "pairs_per_step": pairs, "ms_per_step": ms,
-            "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True}
+            "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True,
+            "phases_ms": {"build": ph[0] / reps, "fwd": ph[1] / reps, "bwd": ph[2] / reps},
+            "cells": [nx, ny, nz], "n_cells": ncells, "cell_split": list(reach)}
 
 
 def also_md(loop_steps=200):

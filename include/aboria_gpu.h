@@ -206,6 +206,22 @@ ab_status ab_pair_sum_bwd(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
                           const float* w, const float* grad_out,
                           float* grad_pos4, float* grad_w, double* grad_s);
 
+/* A pair energy and the gradient of its total in one walk over the pairs:
+ * the loss is L = sum_i E_i, so every upstream gradient is 1 and the forward
+ * and the adjoint can share the predicate and the powers of sig/d (the
+ * common molecular-dynamics step: energies and forces together).
+ *   LJ only.  E (device float32[n], optional): E_i as ab_pair_sum;
+ *   grad_pos4 (device float32[n][4], optional, 16-byte aligned):
+ *     dL/dx_i as ab_pair_sum_bwd with grad_out = 1 (minus the force);
+ *   energy (device float64[1], optional): sum_i E_i.
+ * Bit for bit the results of ab_pair_sum (LJ) and of ab_pair_sum_bwd (LJ)
+ * with a grad_out of ones.
+ * Errors: AB_ERR_UNSUPPORTED (op other than LJ), AB_ERR_STALE,
+ * AB_ERR_INVALID_ARG, AB_ERR_ALIAS (outputs overlap), AB_ERR_OOM,
+ * AB_ERR_CUDA. */
+ab_status ab_pair_energy_grad(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
+                              float* E, float* grad_pos4, double* energy);
+
 /* Export the neighbour relation of the last cell list as CSR in the
  * caller's particle order: offsets (device int64[n+1]) and idx (device
  * int32[cap]) holding original indices of the neighbours of each particle,

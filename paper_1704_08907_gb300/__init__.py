@@ -184,6 +184,25 @@ def ab_pair_sum_bwd(ctx: Context, op, params, w, grad_out, grad_pos4=None, grad_
     return grad_pos4, grad_w, grad_s
 
 
+def ab_pair_energy_grad(ctx: Context, op, params, E=None, grad_pos4=None, energy=None):
+    """Energy and the gradient of the total energy in one walk (LJ):
+    returns (E float32[n], dE_total/dx float32[n,4], total energy float64)."""
+    op = OPS.get(op, op)
+    if E is None:
+        E = torch.empty(ctx.n, dtype=torch.float32, device=ctx.device)
+    if grad_pos4 is None:
+        grad_pos4 = torch.empty((ctx.n, 4), dtype=torch.float32, device=ctx.device)
+    if energy is None:
+        energy = torch.empty((), dtype=torch.float64, device=ctx.device)
+    _dev(E, torch.float32, None, "E")
+    _dev(grad_pos4, torch.float32, (4,), "grad_pos4")
+    _dev(energy, torch.float64, None, "energy")
+    ctx._stream()
+    _check(_lib.ab_pair_energy_grad(ctx.handle, op, ctypes.byref(params), _ptr(E), _ptr(grad_pos4),
+                                    _ptr(energy)), ctx)
+    return E, grad_pos4, energy
+
+
 def ab_pair_list(ctx: Context, cap: int | None = None):
     """Neighbour CSR (offsets int64[n+1], idx int32[nnz]) in caller order."""
     offsets = torch.empty(ctx.n + 1, dtype=torch.int64, device=ctx.device)

@@ -62,6 +62,7 @@ SIGNATURES = {
     "ab_kernel_matvec_bwd": (ST, [P, I64, I64, P, P, I32, P, F32, ctypes.c_int, P,
                                   P, P, P, P]),
     "ab_bd_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, F32, F32, U64, U64]),
+    "ab_pair_energy_grad": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P]),
     "ab_md_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, P, F32]),
     "ab_kernel_solve": (ST, [P, I64, P, I32, P, F32, F32, I32, F32, I32, P,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),

@@ -403,6 +403,39 @@ ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float*
     return AB_OK;
 }
 
+ab_status ab_pair_energy_grad(ab_ctx* c, ab_op op, const ab_op_params* prm, float* E,
+                              float* grad_pos4, double* energy) {
+    if (!c) return AB_ERR_INVALID_ARG;
+    ab_status s = require_cells(c);
+    if (s != AB_OK) return s;
+    if (op != AB_OP_LJ) return fail(c, AB_ERR_UNSUPPORTED, "energy + gradient fused for LJ only");
+    if (!prm) return fail(c, AB_ERR_INVALID_ARG, "params is NULL");
+    const int64_t n = c->cl.n;
+    if (grad_pos4 && !aligned16(grad_pos4))
+        return fail(c, AB_ERR_INVALID_ARG, "grad_pos4 must be 16-byte aligned");
+    if (overlaps(E, (size_t)n * 4, grad_pos4, (size_t)n * 16) ||
+        overlaps(energy, 8, E, (size_t)n * 4) || overlaps(energy, 8, grad_pos4, (size_t)n * 16))
+        return fail(c, AB_ERR_ALIAS, "outputs overlap");
+    cudaSetDevice(c->device);
+    ab::PairOut o;
+    o.out = E;
+    o.grad_pos = (float4*)grad_pos4;
+    const int grid = ab::pair_grid(n);
+    if (energy) {
+        if ((s = ensure_partial(c, (size_t)grid)) != AB_OK) return s;
+        o.partial = c->sc.partial;
+        o.partial_count = grid;
+    }
+    cudaError_t e = ab::launch_pair_energy_grad(c->cl, op, *prm, o, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_energy_grad launch");
+    if (energy) {
+        if (n > 0) e = ab::launch_reduce_partials(o.partial, grid, energy, c->stream);
+        else e = cudaMemsetAsync(energy, 0, sizeof(double), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_energy_grad energy");
+    }
+    return AB_OK;
+}
+
 ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
                           const float* grad_out, float* grad_pos4, float* grad_w,
                           double* grad_s) {

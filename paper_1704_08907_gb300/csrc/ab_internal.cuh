@@ -118,6 +118,11 @@ AB_HIDDEN cudaError_t launch_pair_fwd(const CellList& cl, ab_op op,
 AB_HIDDEN cudaError_t launch_pair_bwd(const CellList& cl, ab_op op,
                                       const ab_op_params& prm, const float2* sv,
                                       PairOut& o, cudaStream_t st);
+// LJ energy + gradient of the total energy in one walk (PairOut out, grad_pos,
+// partial)
+AB_HIDDEN cudaError_t launch_pair_energy_grad(const CellList& cl, ab_op op,
+                                              const ab_op_params& prm, PairOut& o,
+                                              cudaStream_t st);
 AB_HIDDEN cudaError_t launch_pair_count(const CellList& cl, uint32_t* counts,
                                         cudaStream_t st);
 AB_HIDDEN cudaError_t launch_pair_emit(const CellList& cl, const int64_t* offsets,

@@ -417,6 +417,41 @@ k_pair_bwd(PairParams P, PairOut o) {
         block_partial<kPairThreads>(live ? -(double)vi.y * (double)ds : 0.0, o.partial);
 }
 
+// LJ energy and its gradient in one walk, for a loss equal to the total
+// energy (every per-particle energy has upstream gradient 1): the forward's
+// E_i = 1/2 eps sum_j ((sig/d)^12 - (sig/d)^6) and the adjoint's
+// dE/dx_i = eps sum_j (g_i + g_j) C_ij dx_ij with g = 1, sharing the
+// predicate and the powers of sig/d.  Bit for bit the results of k_pair_fwd_q
+// (LJ) and of k_pair_bwd (LJ) with g = 1: the same visit order, the same
+// expressions, and (g_i + g_j) = 2 exactly.
+template <int DIM, bool GENERAL>
+__global__ void __launch_bounds__(kPairThreads, 8)
+k_pair_lj_eg(PairParams P, PairOut o) {
+    const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
+    const bool live = s < P.n;
+    const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float e = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+    if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
+        [&](uint32_t, const float4&, float dx, float dy, float dz, float d2) {
+            const float inv = rcp_approx(d2);
+            const float sr2 = P.sig2 * inv;
+            const float sr6 = sr2 * sr2 * sr2;
+            e = fmaf(sr6, sr6 - 1.0f, e);
+            const float coef = 2.0f * (sr6 * fmaf(6.0f, sr6, -3.0f)) * inv;
+            gx = fmaf(coef, dx, gx);
+            gy = fmaf(coef, dy, gy);
+            gz = fmaf(coef, dz, gz);
+        });
+    if (live) {
+        const uint32_t p = __ldg(P.perm + s);
+        e *= 0.5f * P.eps;
+        if (o.out) o.out[p] = e;
+        if (o.grad_pos)
+            o.grad_pos[p] = make_float4(P.eps * gx, P.eps * gy, DIM == 3 ? P.eps * gz : 0.0f, 0.0f);
+    }
+    if (o.partial) block_partial<kPairThreads>(live ? (double)e : 0.0, o.partial);
+}
+
 template <int DIM, bool GENERAL>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
@@ -514,6 +549,15 @@ cudaError_t launch_pair_bwd(const CellList& cl, ab_op op, const ab_op_params& pr
         case AB_OP_LJ: AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_LJ), P, o); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_energy_grad(const CellList& cl, ab_op op, const ab_op_params& prm,
+                                   PairOut& o, cudaStream_t st) {
+    if (cl.n <= 0) return cudaSuccess;
+    if (op != AB_OP_LJ) return cudaErrorNotSupported;
+    PairParams P = make_params(cl, prm, nullptr);
+    AB_DISPATCH_DG(k_pair_lj_eg, kPairThreads, , P, o);
     return cudaGetLastError();
 }
 
