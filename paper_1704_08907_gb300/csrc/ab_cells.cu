@@ -148,10 +148,26 @@ k_scan(const uint32_t* in, TOut* out, int64_t n, uint64_t* status,
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    // 16-byte vector accesses when the arrays allow them (in and out may be
+    // the same array: every thread reads its items before writing them)
+    const bool whole = base + kScanItems <= n;
+    const bool vec_in = whole && (((uintptr_t)in & 15u) == 0);
+    const bool vec_out = whole && sizeof(TOut) == 4 && (((uintptr_t)out & 15u) == 0);
 
     uint32_t v[kScanItems];
+    if (vec_in) {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 t = reinterpret_cast<const uint4*>(in + base)[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+    }
     uint64_t tsum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) tsum += v[k];
@@ -179,40 +195,64 @@ k_scan(const uint32_t* in, TOut* out, int64_t n, uint64_t* status,
     const uint64_t block_total = s_warp[kThreads / 32 - 1];
     const uint64_t warp_excl = warp ? s_warp[warp - 1] : 0;
 
-    if (threadIdx.x == 0) {
+    // decoupled look-back by warp 0: lane l reads the status word of tile
+    // j - l, so 32 predecessors are examined per poll; the exclusive prefix is
+    // the sum of the values from tile - 1 down to the nearest tile that has
+    // published its inclusive prefix (a tile before tile 0 counts as prefix 0)
+    if (warp == 0) {
         uint64_t excl = 0;
         if (tile == 0) {
-            if (tile != skip_tile) st_release(status, kFlagPre | (block_total & kValMask));
+            if (lane == 0 && tile != skip_tile) st_release(status, kFlagPre | (block_total & kValMask));
         } else {
-            if (tile != skip_tile) st_release(status + tile, kFlagAgg | (block_total & kValMask));
+            if (lane == 0 && tile != skip_tile)
+                st_release(status + tile, kFlagAgg | (block_total & kValMask));
             const long long t0 = global_ns();
             int64_t j = tile - 1;
-            while (j >= 0) {
-                uint64_t w = ld_acquire(status + j);
-                uint64_t f = w & ~kValMask;
-                if (f == 0) {
+            for (;;) {
+                const int64_t idx = j - lane;
+                const uint64_t w = idx >= 0 ? ld_acquire(status + idx) : kFlagPre;
+                const uint64_t f = w & ~kValMask;
+                const unsigned pre = __ballot_sync(0xffffffffu, f == kFlagPre);
+                const unsigned zero = __ballot_sync(0xffffffffu, f == 0);
+                const int first = pre ? __ffs(pre) - 1 : 31;
+                const unsigned upto = first == 31 ? 0xffffffffu : ((1u << (first + 1)) - 1u);
+                if (zero & upto) {   // a tile in the window has not published yet
                     if (global_ns() - t0 > limit_ns) {
-                        atomicOr(err, DEVERR_SCAN_TIMEOUT);
+                        if (lane == 0) atomicOr(err, DEVERR_SCAN_TIMEOUT);
                         break;
                     }
-                    __nanosleep(64);
                     continue;
                 }
-                excl += w & kValMask;
-                if (f == kFlagPre) break;
-                --j;
+                uint64_t part = ((upto >> lane) & 1u) ? (w & kValMask) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                if (pre) break;
+                j -= 32;
             }
-            if (tile != skip_tile)
+            if (lane == 0 && tile != skip_tile)
                 st_release(status + tile, kFlagPre | ((excl + block_total) & kValMask));
         }
-        s_prefix = excl;
+        if (lane == 0) s_prefix = excl;
     }
     __syncthreads();
     uint64_t run = s_prefix + warp_excl + (incl - tsum);
+    if (vec_out) {
+        uint32_t o[kScanItems];
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = (TOut)run;
-        run += v[k];
+        for (int k = 0; k < kScanItems; ++k) {
+            o[k] = (uint32_t)run;
+            run += v[k];
+        }
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q)
+            reinterpret_cast<uint4*>(out + base)[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < n) out[base + k] = (TOut)run;
+            run += v[k];
+        }
     }
 }
 
