@@ -42,7 +42,8 @@ namespace {
 
 constexpr int kTM = 128;            // rows of X per CTA (= TMEM lanes)
 constexpr int kRhs = 64;            // MMA N
-constexpr int kStages = 3;          // W ring depth
+constexpr int kStages = 3;          // G/W ring depth of the adjoint
+constexpr int kFwdStages = 3;       // W ring depth of the forward
 // A W tile is 64 rows x 256 bytes of K in either precision: 128 bf16 points
 // or 64 tf32 points.  Its P block is 64 TMEM columns either way.
 constexpr int kTileBytes = kRhs * 256;              // one hi or lo image: 16 KB
@@ -69,10 +70,10 @@ constexpr float kLog2eTC = 1.4426950408889634f;
 struct SmemLayout {
     // W ring first: each stage must be 1024-byte aligned for the swizzle atoms
     static constexpr int w = 0;
-    static constexpr int bars = kStages * kStageBytesMax;       // <= 102 KB
-    static constexpr int full = bars;                           // [kStages]
-    static constexpr int empty = full + 8 * kStages;            // [kStages]
-    static constexpr int pfull = empty + 8 * kStages;           // [kPBufs]
+    static constexpr int bars = kFwdStages * kStageBytesMax;       // <= 102 KB
+    static constexpr int full = bars;                           // [kFwdStages]
+    static constexpr int empty = full + 8 * kFwdStages;            // [kFwdStages]
+    static constexpr int pfull = empty + 8 * kFwdStages;           // [kPBufs]
     static constexpr int pempty = pfull + 8 * kPBufs;           // [kPBufs]
     static constexpr int accfull = pempty + 8 * kPBufs;
     static constexpr int tmem_slot = accfull + 8;
@@ -81,7 +82,10 @@ struct SmemLayout {
 };
 // + alignment slack; rounded up past half of the SM's 228 KB so that only
 // one CTA is resident per SM (each CTA allocates all 512 TMEM columns)
-constexpr int kSmemBytes = 120 * 1024;
+constexpr int kSmemBytes = SmemLayout::bytes + 1024 > 120 * 1024
+                               ? (SmemLayout::bytes + 1024 + 1023) / 1024 * 1024
+                               : 120 * 1024;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
 static_assert(SmemLayout::bytes + 1024 <= kSmemBytes, "shared memory layout");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -184,6 +188,16 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+}
+// 16 lanes x 16 columns: thread t holds, per 8-column repetition r,
+// v[4r + 0, 1] = lane t/4, columns 8r + 2 (t%4) + {0, 1} and
+// v[4r + 2, 3] = lane t/4 + 8, the same columns.
+__device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+            taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
         : "memory");
 }
@@ -374,8 +388,14 @@ k_bbox(int64_t n, const float4* __restrict__ Y, uint32_t* __restrict__ bbox) {
 // FP32 rounding of the expanded form stays ~1e-5 in the exponent.  Padding
 // points get yhat = (0, 0, 0, -inf): their kernel values are exactly 0.
 // Layout: points in pairs (2p, 2p+1), each pair as two float4
-//   (x0, x1, y0, y1), (z0, z1, w0, w1)
+//   A = (x0, x1, y0, y1), B = (z0, z1, w0, w1)
 // so the epilogue loads a column pair's components as packed FP32 pairs.
+// BLOCKED (bf16 tiles): within each block of 16 points (pairs 2c + e,
+// c = 0..3, e = 0..1) the float4 at 16 * block + 4 * (2 e + {A: 0, B: 1}) + c,
+// so that the four column quads c of one 16-point block, read by the four
+// threads of a TMEM lane group at once, are 64 contiguous bytes (no bank
+// conflict).  Otherwise pair p at float4 2p (A) and 2p + 1 (B).
+template <bool BLOCKED>
 __global__ void __launch_bounds__(256)
 k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* __restrict__ bbox,
          float sl2e, float4* __restrict__ Yhat, float4* __restrict__ centre) {
@@ -398,8 +418,15 @@ k_prep_y(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* 
                 h[u] = make_float4(0.0f, 0.0f, 0.0f, -__int_as_float(0x7f800000));
             }
         }
-        Yhat[2 * p] = make_float4(h[0].x, h[1].x, h[0].y, h[1].y);
-        Yhat[2 * p + 1] = make_float4(h[0].z, h[1].z, h[0].w, h[1].w);
+        int64_t ia = 2 * p, ib = 2 * p + 1;
+        if (BLOCKED) {
+            const int64_t blk = p >> 3;
+            const int c = (int)(p >> 1) & 3, e = (int)p & 1;
+            ia = 16 * blk + 4 * (2 * e) + c;
+            ib = 16 * blk + 4 * (2 * e + 1) + c;
+        }
+        Yhat[ia] = make_float4(h[0].x, h[1].x, h[0].y, h[1].y);
+        Yhat[ib] = make_float4(h[0].z, h[1].z, h[0].w, h[1].w);
     }
 }
 
@@ -431,7 +458,7 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kFwdStages; ++s) {
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1 + kEpiWarps);   // MMA commit + one per epilogue warp
         }
@@ -461,9 +488,9 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         if (lane == 0) {
             int64_t issued = 0;
             for (int64_t t = 0; t < tiles; ++t) {
-                const int s = (int)(t % kStages);
-                const uint32_t use = (uint32_t)(t / kStages);
-                if (t >= kStages && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, abort_flag, err))
+                const int s = (int)(t % kFwdStages);
+                const uint32_t use = (uint32_t)(t / kFwdStages);
+                if (t >= kFwdStages && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, abort_flag, err))
                     break;
                 const int64_t gt = t_begin + t;
                 mbar_arrive_expect_tx(bar_full + 8 * s, kStageBytes);
@@ -474,10 +501,10 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 issued = t + 1;
             }
             // copies still in flight must land before the CTA may exit
-            for (int64_t t = issued > kStages ? issued - kStages : 0; t < issued; ++t) {
-                const int s = (int)(t % kStages);
+            for (int64_t t = issued > kFwdStages ? issued - kFwdStages : 0; t < issued; ++t) {
+                const int s = (int)(t % kFwdStages);
                 const long long t0 = gtimer();
-                while (!mbar_try_wait(bar_full + 8 * s, (uint32_t)(t / kStages) & 1)) {
+                while (!mbar_try_wait(bar_full + 8 * s, (uint32_t)(t / kFwdStages) & 1)) {
                     if (gtimer() - t0 > kWaitLimitNs) {
                         atomicOr(err, DEVERR_TC_TIMEOUT);
                         break;
@@ -489,9 +516,9 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             for (int64_t t = 0; t < tiles; ++t) {
-                const int s = (int)(t % kStages);
+                const int s = (int)(t % kFwdStages);
                 const int b = (int)(t % kPBufs);
-                if (!mbar_wait(bar_full + 8 * s, (uint32_t)(t / kStages) & 1, abort_flag, err)) break;
+                if (!mbar_wait(bar_full + 8 * s, (uint32_t)(t / kFwdStages) & 1, abort_flag, err)) break;
                 if (!mbar_wait(bar_pfull + 8 * b, (uint32_t)(t / kPBufs) & 1, abort_flag, err)) break;
                 tc_fence_after();
                 const uint32_t a_hi = tmem + kColP + 128 * b;
@@ -544,6 +571,30 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         }
         const uint64_t xa2 = f2pack(xa, xa), xb2 = f2pack(xb, xb), xc2 = f2pack(xc, xc);
         const uint64_t ci2 = f2pack(ci, ci);
+        // bf16 paths: thread (g4, c4) = (lane / 4, lane % 4) evaluates rows
+        // 8 r + g4 (r = 0..3) of its quadrant at column quads c4, so one
+        // yhat load serves four rows (the 16x256b TMEM store layout)
+        const int g4 = lane >> 2, c4 = lane & 3;
+        uint64_t xq[4][4];   // row r: xa, xb, xc, ci as duplicated pairs
+        if (!TF32) {
+            const float4 c = __ldg(centre);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t row = row0 + quad * 32 + 8 * r + g4;
+                float a = 0.f, bb = 0.f, cc = 0.f, ck = -__int_as_float(0x7f800000);
+                if (row < m) {
+                    const float4 x = __ldg(X + row);
+                    a = x.x - c.x;
+                    bb = x.y - c.y;
+                    cc = x.z - c.z;
+                    ck = -sl2e * fmaf(cc, cc, fmaf(bb, bb, a * a));
+                }
+                xq[r][0] = f2pack(a, a);
+                xq[r][1] = f2pack(bb, bb);
+                xq[r][2] = f2pack(cc, cc);
+                xq[r][3] = f2pack(ck, ck);
+            }
+        }
         for (int64_t t = 0; t < tiles; ++t) {
             const int b = (int)(t % kPBufs);
             if (t >= kPBufs) {
@@ -551,9 +602,9 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                                           abort_flag, err);
                 if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
             }
-            const int st = (int)(t % kStages);
+            const int st = (int)(t % kFwdStages);
             {
-                const bool ok = mbar_wait(bar_full + 8 * st, (uint32_t)(t / kStages) & 1, abort_flag, err);
+                const bool ok = mbar_wait(bar_full + 8 * st, (uint32_t)(t / kFwdStages) & 1, abort_flag, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
             tc_fence_after();
@@ -596,31 +647,50 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 tmem_st16(lane_base + col, hi);
                 if (SPLIT) tmem_st16(lane_base + col + 64, lo);
             } else {
+                // two 16-column blocks; per block four 16-byte yhat loads
+                // (column pairs 2 c4 and 2 c4 + 1, parts A and B) serve
+                // 4 rows x 4 columns
+                uint32_t hi[2][8], lo[2][8];   // [lane half][16x256b register]
 #pragma unroll
-                for (int c0 = 0; c0 < kColsPerWarp; c0 += 16) {
-                    uint32_t hi[8], lo[8];
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t yb = yt + 256 * k + 16 * c4;
+                    const float4 Ae = lds128(yb), Be = lds128(yb + 64);
+                    const float4 Ao = lds128(yb + 128), Bo = lds128(yb + 192);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float e0, e1;
-                        exponent2(c0 / 2 + q, e0, e1);
-                        const float p0 = ex2f_tc(e0), p1 = ex2f_tc(e1);
-                        if (SPLIT) {
-                            // hi = top 16 bits of p (truncation, integer ops only:
-                            // the conversion unit is already busy with ex2), lo =
-                            // p - hi exactly, then its top 16 bits: relative
-                            // error <= 2^-16 of p
-                            const uint32_t b0 = __float_as_uint(p0), b1 = __float_as_uint(p1);
-                            const float r0 = p0 - __uint_as_float(b0 & 0xFFFF0000u);
-                            const float r1 = p1 - __uint_as_float(b1 & 0xFFFF0000u);
-                            hi[q] = __byte_perm(b0, b1, 0x7632);
-                            lo[q] = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
-                        } else {
-                            hi[q] = pack_bf16x2(p0, p1);
+                    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                        for (int jp = 0; jp < 2; ++jp) {
+                            const float4 A = jp ? Ao : Ae, B = jp ? Bo : Be;
+                            uint64_t e = add2(f2pack(B.z, B.w), xq[r][3]);
+                            e = fma2(xq[r][2], f2pack(B.x, B.y), e);
+                            e = fma2(xq[r][1], f2pack(A.z, A.w), e);
+                            e = fma2(xq[r][0], f2pack(A.x, A.y), e);
+                            float e0, e1;
+                            f2unpack(e, e0, e1);
+                            const float p0 = ex2f_tc(e0), p1 = ex2f_tc(e1);
+                            const int q = 4 * k + 2 * (r & 1) + jp;
+                            if (SPLIT) {
+                                // hi = top 16 bits of p (truncation, integer ops only:
+                                // the conversion unit is already busy with ex2), lo =
+                                // p - hi exactly, then its top 16 bits: relative
+                                // error <= 2^-16 of p
+                                const uint32_t b0 = __float_as_uint(p0), b1 = __float_as_uint(p1);
+                                const float r0 = p0 - __uint_as_float(b0 & 0xFFFF0000u);
+                                const float r1 = p1 - __uint_as_float(b1 & 0xFFFF0000u);
+                                hi[r >> 1][q] = __byte_perm(b0, b1, 0x7632);
+                                lo[r >> 1][q] = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
+                            } else {
+                                hi[r >> 1][q] = pack_bf16x2(p0, p1);
+                            }
                         }
                     }
-                    const uint32_t col = kColP + 128 * b + (part * kColsPerWarp + c0) / 2;
-                    tmem_st8(lane_base + col, hi);
-                    if (SPLIT) tmem_st8(lane_base + col + 64, lo);
+                }
+                const uint32_t col = kColP + 128 * b + part * (kColsPerWarp / 2);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t ta = lane_base + ((uint32_t)(16 * h) << 16) + col;
+                    tmem_st_16x256b_x2(ta, hi[h]);
+                    if (SPLIT) tmem_st_16x256b_x2(ta + 64, lo[h]);
                 }
             }
             tmem_wait_st();
@@ -1022,8 +1092,8 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const float sl2e = s * kLog2eTC;
-    k_prep_y<<<(unsigned)((tiles * TN / 2 + 255) / 256), 256, 0, st>>>(n, Y, tiles * TN, bbox, sl2e, Yhat,
-                                                                   centre);
+    k_prep_y<!TF32><<<(unsigned)((tiles * TN / 2 + 255) / 256), 256, 0, st>>>(n, Y, tiles * TN, bbox, sl2e,
+                                                                          Yhat, centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t mblocks = (m + kTM - 1) / kTM;
     // split the Y range in two when the row blocks alone leave a ragged last
