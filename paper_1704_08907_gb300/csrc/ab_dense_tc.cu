@@ -70,7 +70,7 @@ constexpr float kLog2eTC = 1.4426950408889634f;
 struct SmemLayout {
     // W ring first: each stage must be 1024-byte aligned for the swizzle atoms
     static constexpr int w = 0;
-    static constexpr int bars = kFwdStages * kStageBytesMax;       // <= 102 KB
+    static constexpr int bars = kFwdStages * kStageBytesMax;    // 102 KB at 3 stages
     static constexpr int full = bars;                           // [kFwdStages]
     static constexpr int empty = full + 8 * kFwdStages;            // [kFwdStages]
     static constexpr int pfull = empty + 8 * kFwdStages;           // [kPBufs]
@@ -183,12 +183,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
         "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
         "r"(v[15])
-        : "memory");
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
         : "memory");
 }
 // 16 lanes x 16 columns: thread t holds, per 8-column repetition r,
@@ -595,16 +589,17 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 xq[r][3] = f2pack(ck, ck);
             }
         }
+        // ring positions and phase parities kept incrementally: a 64-bit
+        // division per tile costs ~10% of the epilogue's issue slots
+        int b = 0, st = 0;
+        uint32_t pround = 0, sround = 0;   // (t / kPBufs) & 1, (t / kFwdStages) & 1
         for (int64_t t = 0; t < tiles; ++t) {
-            const int b = (int)(t % kPBufs);
             if (t >= kPBufs) {
-                const bool ok = mbar_wait(bar_pempty + 8 * b, (uint32_t)((t - kPBufs) / kPBufs) & 1,
-                                          abort_flag, err);
+                const bool ok = mbar_wait(bar_pempty + 8 * b, pround ^ 1u, abort_flag, err);
                 if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
             }
-            const int st = (int)(t % kFwdStages);
             {
-                const bool ok = mbar_wait(bar_full + 8 * st, (uint32_t)(t / kFwdStages) & 1, abort_flag, err);
+                const bool ok = mbar_wait(bar_full + 8 * st, sround, abort_flag, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
             tc_fence_after();
@@ -698,6 +693,8 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             mbar_arrive(bar_pfull + 8 * b);
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_empty + 8 * st);   // this warp is done with yhat
+            if (++b == kPBufs) { b = 0; pround ^= 1u; }
+            if (++st == kFwdStages) { st = 0; sround ^= 1u; }
         }
         // accumulator ready (or aborted: the wait is still bounded)
         bool ok = mbar_wait(bar_acc, 0, abort_flag, err);
@@ -980,11 +977,12 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         }
         const float xh0 = 2.0f * sl2e * xt0, xh1 = 2.0f * sl2e * xt1, xh2 = 2.0f * sl2e * xt2;
         float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
+        int q = 0;
+        uint32_t qround = 0;   // ring position t % kStages and parity (t / kStages) & 1
         for (int64_t t = 0; t < tiles; ++t) {
-            const int q = (int)(t % kStages);
             const int b = (int)(t & 1);
             bool ok = mbar_wait(bar_sfull + 8 * b, (uint32_t)(t >> 1) & 1, abort_flag, err);
-            ok = ok && mbar_wait(bar_full + 8 * q, (uint32_t)(t / kStages) & 1, abort_flag, err);
+            ok = ok && mbar_wait(bar_full + 8 * q, qround, abort_flag, err);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             const uint32_t yt = sbase + GradSmem::ring + q * kGStage + kGImg + part * 32 * 16;
@@ -1010,6 +1008,7 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 mbar_arrive(bar_sempty + 8 * b);
                 mbar_arrive(bar_empty + 8 * q);
             }
+            if (++q == kStages) { q = 0; qround ^= 1u; }
         }
         // combine the four column slices of each row, then write
         float* red = (float*)(smem + GradSmem::red);
