@@ -195,6 +195,18 @@ __device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, const uint32_
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
         : "memory");
 }
+// 16 lanes x 32 columns, the load counterpart of tmem_st_16x256b_x2 (four
+// 8-column repetitions of four registers each).
+__device__ __forceinline__ void tmem_ld_16x256b_x4(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -256,6 +268,11 @@ __device__ __forceinline__ void f2unpack(uint64_t v, float& a, float& b) {
 __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
@@ -825,25 +842,31 @@ k_prep_rows64(int64_t rows, int ncols, const float* __restrict__ src, int64_t bl
     }
 }
 
-// Centred points for the gradient: (y - c, -s' |y - c|^2); padding points
-// get (0, 0, 0, -1e30): their kernel value is 0 and, unlike -inf, the
-// exponent times A = 0 stays 0 in the ds sum.
+// Centred points for the gradient, y~ = y - c, in pairs (2p, 2p + 1) as two
+// float4 (x0, x1, y0, y1), (z0, z1, 0, 0), so the epilogue reads a column
+// pair's components as packed FP32 pairs.  Padding points are 0; their
+// column of S = G W^T is exactly 0 (zero rows of W), so they add nothing.
 __global__ void __launch_bounds__(256)
 k_prep_ytil(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* __restrict__ bbox,
-            float sl2e, float4* __restrict__ Yt, float4* __restrict__ centre) {
+            float4* __restrict__ Yt, float4* __restrict__ centre) {
     const float c0 = 0.5f * (ord2f(bbox[0]) + ord2f(bbox[4]));
     const float c1 = 0.5f * (ord2f(bbox[1]) + ord2f(bbox[5]));
     const float c2 = 0.5f * (ord2f(bbox[2]) + ord2f(bbox[6]));
     if (blockIdx.x == 0 && threadIdx.x == 0) *centre = make_float4(c0, c1, c2, 0.0f);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        if (j < n) {
-            const float4 y = __ldg(Y + j);
-            const float a = y.x - c0, b = y.y - c1, c = y.z - c2;
-            Yt[j] = make_float4(a, b, c, -sl2e * fmaf(c, c, fmaf(b, b, a * a)));
-        } else {
-            Yt[j] = make_float4(0.0f, 0.0f, 0.0f, -1e30f);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 2 * p < npad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float3 h[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t j = 2 * p + u;
+            h[u] = make_float3(0.0f, 0.0f, 0.0f);
+            if (j < n) {
+                const float4 y = __ldg(Y + j);
+                h[u] = make_float3(y.x - c0, y.y - c1, y.z - c2);
+            }
         }
+        Yt[2 * p] = make_float4(h[0].x, h[1].x, h[0].y, h[1].y);
+        Yt[2 * p + 1] = make_float4(h[0].z, h[1].z, 0.0f, 0.0f);
     }
 }
 
@@ -964,19 +987,43 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             tc_commit(bar_done);
         }
     } else {
-        const int quad = warp & 3, part = warp >> 2;
-        const int i = quad * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-        float xt0 = 0.f, xt1 = 0.f, xt2 = 0.f, ci = -1e30f;   // padding row: K = 0
-        if (row0 + i < m) {
-            const float4 x = __ldg(X + row0 + i), c = __ldg(centre);
-            xt0 = x.x - c.x;
-            xt1 = x.y - c.y;
-            xt2 = x.z - c.z;
-            ci = -sl2e * fmaf(xt2, xt2, fmaf(xt1, xt1, xt0 * xt0));
+        // Warp w serves TMEM lane quadrant w % 4, lane half (w / 4) % 2 and
+        // columns 64 (w / 8) .. +63 of each S tile.  Thread (g4, c4) =
+        // (lane / 4, lane % 4) holds rows 16 h + 8 u + g4 (u = 0, 1) of the
+        // quadrant at column pairs 8 k + 2 c4 (the 16x256b TMEM load layout):
+        // one y~ load serves two rows, and every step works on column pairs
+        // with packed FP32 arithmetic.  The exponent is formed from the
+        // differences d = x~ - y~ that the sums need anyway:
+        // -s' |d|^2 (base 2), K = 2^that.
+        const int quad = warp & 3, half = (warp >> 2) & 1, cpart = warp >> 3;
+        const int g4 = lane >> 2, c4 = lane & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32 + 16 * half) << 16);
+        uint64_t xt[2][3];   // row u: x~ components as duplicated pairs (padding rows: S = 0)
+        {
+            const float4 c = __ldg(centre);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t row = row0 + quad * 32 + 16 * half + 8 * u + g4;
+                float a = 0.f, bb = 0.f, cc = 0.f;
+                if (row < m) {
+                    const float4 x = __ldg(X + row);
+                    a = x.x - c.x;
+                    bb = x.y - c.y;
+                    cc = x.z - c.z;
+                }
+                xt[u][0] = f2pack(a, a);
+                xt[u][1] = f2pack(bb, bb);
+                xt[u][2] = f2pack(cc, cc);
+            }
         }
-        const float xh0 = 2.0f * sl2e * xt0, xh1 = 2.0f * sl2e * xt1, xh2 = 2.0f * sl2e * xt2;
-        float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
+        const uint64_t nsl2 = f2pack(-sl2e, -sl2e);
+        // per row: sums of A dx, A dy, A dz and A * exponent, even and odd
+        // columns in the two halves of each packed pair
+        uint64_t acc[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[u][k] = 0ull;
         int q = 0;
         uint32_t qround = 0;   // ring position t % kStages and parity (t / kStages) & 1
         for (int64_t t = 0; t < tiles; ++t) {
@@ -985,21 +1032,35 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             ok = ok && mbar_wait(bar_full + 8 * q, qround, abort_flag, err);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            const uint32_t yt = sbase + GradSmem::ring + q * kGStage + kGImg + part * 32 * 16;
+            // pair record (64 cpart + 8 k + c0) / 2 + c4 of this tile's y~
+            const uint32_t yt = sbase + GradSmem::ring + q * kGStage + kGImg + cpart * 64 * 16 + 32 * c4;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 32; c0 += 16) {
+            for (int c0 = 0; c0 < 64; c0 += 32) {
                 uint32_t v[16];
-                tmem_ld16(lane_base + 128 * b + part * 32 + c0, v);
+                tmem_ld_16x256b_x4(lane_base + 128 * b + cpart * 64 + c0, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float4 y = lds128(yt + 16 * (c0 + k));
-                    const float e = fmaf(xh0, y.x, fmaf(xh1, y.y, fmaf(xh2, y.z, y.w))) + ci;
-                    const float A = __uint_as_float(v[k]) * ex2f_tc(e);
-                    ax = fmaf(A, xt0 - y.x, ax);
-                    ay = fmaf(A, xt1 - y.y, ay);
-                    az = fmaf(A, xt2 - y.z, az);
-                    ae = fmaf(A, e, ae);
+                for (int k = 0; k < 4; ++k) {
+                    const float4 P = lds128(yt + 16 * (c0 + 8 * k)), Q = lds128(yt + 16 * (c0 + 8 * k) + 16);
+                    const uint64_t yx = f2pack(P.x, P.y), yy = f2pack(P.z, P.w), yz = f2pack(Q.x, Q.y);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const uint64_t d0 = sub2(xt[u][0], yx), d1 = sub2(xt[u][1], yy);
+                        const uint64_t d2 = sub2(xt[u][2], yz);
+                        uint64_t e = mul2(d0, d0);
+                        e = fma2(d1, d1, e);
+                        e = fma2(d2, d2, e);
+                        e = mul2(e, nsl2);
+                        float e0, e1;
+                        f2unpack(e, e0, e1);
+                        const uint64_t A = mul2(f2pack(__uint_as_float(v[4 * k + 2 * u]),
+                                                       __uint_as_float(v[4 * k + 2 * u + 1])),
+                                                f2pack(ex2f_tc(e0), ex2f_tc(e1)));
+                        acc[u][0] = fma2(A, d0, acc[u][0]);
+                        acc[u][1] = fma2(A, d1, acc[u][1]);
+                        acc[u][2] = fma2(A, d2, acc[u][2]);
+                        acc[u][3] = fma2(A, e, acc[u][3]);
+                    }
                 }
             }
             tc_fence_before();
@@ -1010,12 +1071,22 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             }
             if (++q == kStages) { q = 0; qround ^= 1u; }
         }
-        // combine the four column slices of each row, then write
+        // fold each row's column pairs and its four column-quad lanes, then
+        // combine the two column halves of the tile through shared memory
         float* red = (float*)(smem + GradSmem::red);
-        red[(part * 128 + i) * 4 + 0] = ax;
-        red[(part * 128 + i) * 4 + 1] = ay;
-        red[(part * 128 + i) * 4 + 2] = az;
-        red[(part * 128 + i) * 4 + 3] = ae;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = quad * 32 + 16 * half + 8 * u + g4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float lo, hi;
+                f2unpack(acc[u][k], lo, hi);
+                float v = lo + hi;
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                if (c4 == 0) red[(cpart * 128 + i) * 4 + k] = v;
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -1024,7 +1095,7 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         const int i = threadIdx.x;
         float sx = 0.f, sy = 0.f, sz = 0.f, se = 0.f;
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) {
+        for (int pp = 0; pp < 2; ++pp) {
             sx += red[(pp * 128 + i) * 4 + 0];
             sy += red[(pp * 128 + i) * 4 + 1];
             sz += red[(pp * 128 + i) * 4 + 2];
@@ -1149,7 +1220,7 @@ cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* X, const f
     k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const float sl2e = s * kLog2eTC;
-    k_prep_ytil<<<(unsigned)((nb * 128 + 255) / 256), 256, 0, st>>>(n, Y, nb * 128, bbox, sl2e, Yt, centre);
+    k_prep_ytil<<<(unsigned)((nb * 64 + 255) / 256), 256, 0, st>>>(n, Y, nb * 128, bbox, Yt, centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int split = (mb < 4 * (int64_t)g_num_sms && nb >= 2) ? 2 : 1;
     if (split == 2 && dX && (e = cudaMemsetAsync(dX, 0, (size_t)m * sizeof(float4), st)) != cudaSuccess)
