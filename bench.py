@@ -754,8 +754,14 @@ def probe(spec):
     Y = torch.from_numpy(synth.pack4(d.Y)).cuda()
     W = torch.from_numpy(d.W).cuda()
     ctx = ab.Context(0)
-    for prec in items.split(","):
-        ab.ab_kernel_matvec(ctx, X, Y, W, d.s, prec)
+    for item in items.split(","):
+        if item.startswith("bwd-"):   # adjoint: dW (forward kernel), dX and dY (gradient kernel)
+            G = torch.from_numpy(d.G).cuda()
+            ab.ab_kernel_matvec_bwd(ctx, X, Y, W, d.s, item[4:], G, torch.empty_like(W),
+                                    torch.empty_like(X), torch.empty_like(Y),
+                                    torch.empty((), dtype=torch.float64, device="cuda"))
+        else:
+            ab.ab_kernel_matvec(ctx, X, Y, W, d.s, item)
     ab.ab_sync(ctx)
     torch.cuda.synchronize()
     ctx.close()
