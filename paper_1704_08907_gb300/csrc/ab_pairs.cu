@@ -437,7 +437,10 @@ k_pair_lj_eg(PairParams P, PairOut o) {
             const float sr2 = P.sig2 * inv;
             const float sr6 = sr2 * sr2 * sr2;
             e = fmaf(sr6, sr6 - 1.0f, e);
-            const float coef = 2.0f * (sr6 * fmaf(6.0f, sr6, -3.0f)) * inv;
+            // (g_i + g_j) (sr6 (6 sr6 - 3)) / d2 with g = 1: the factor 2 is
+            // folded into the fma, exactly (scaling by 2 commutes with
+            // rounding; 6 sr6 - 3 is 0 or far from the subnormal range)
+            const float coef = (sr6 * fmaf(12.0f, sr6, -6.0f)) * inv;
             gx = fmaf(coef, dx, gx);
             gy = fmaf(coef, dy, gy);
             gz = fmaf(coef, dz, gz);
