@@ -273,16 +273,18 @@ def run_ours(args, rank, world):
     else:
         value = pairs * args.steps / (total_ms * 1e-3)
 
-    # end to end through the public API with host buffers
-    pos_h = torch.from_numpy(w.pos).pin_memory()
-    F_h = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    # end to end through the public API with host buffers: coordinates packed
+    # as xyz (12 bytes a particle) both ways, the layout a caller's arrays have
+    pos_h = torch.from_numpy(np.ascontiguousarray(w.pos[:, :3])).pin_memory()
+    F_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
     e_h = torch.empty((), dtype=torch.float64).pin_memory()
-    pos_d = torch.empty_like(pos)
+    pos_d = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    F3 = torch.empty((n, 3), dtype=torch.float32, device=dev)
 
     def e2e_step():
         pos_d.copy_(pos_h, non_blocking=True)
-        ab.lj_energy_forces(ctx, dom, pos_d, eps, sigma, E=E, F=F, energy=etot)
-        F_h.copy_(F, non_blocking=True)
+        ab.lj_energy_forces(ctx, dom, pos_d, eps, sigma, E=E, F=F3, energy=etot)
+        F_h.copy_(F3, non_blocking=True)
         e_h.copy_(etot, non_blocking=True)
 
     for _ in range(args.warmup):
@@ -343,7 +345,8 @@ def run_ours(args, rank, world):
             "fwd_alu_frac": fwd_ops / (float(np.mean(u_fwd)) * 1e-3) / 1e12 / alu_peak,
             "bwd_alu_frac": bwd_ops / (float(np.mean(u_bwd)) * 1e-3) / 1e12 / alu_peak},
         "e2e": {"value": pairs * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16 + 8},
+                "h2d_bytes_per_step": pos_h.numel() * 4,
+                "d2h_bytes_per_step": F_h.numel() * 4 + 8},
         "gpu_launches": 6 * args.steps,
         "wall_s": wall,
     }

@@ -150,6 +150,15 @@ ab_status ab_sync(ab_ctx* ctx);
 ab_status ab_build(ab_ctx* ctx, const ab_domain* dom, int64_t n,
                    const float* pos4);
 
+/* ab_build for positions packed as dom->dim floats per particle
+ * (float32[n][3] in 3-D, float32[n][2] in 2-D, device, 4-byte aligned): the
+ * layout arrays of coordinates usually have, a quarter (3-D) or half (2-D)
+ * fewer bytes to bring to the device than pos4.  The cell list, and every
+ * later result, is bit for bit that of ab_build on the same coordinates.
+ * Errors as ab_build (AB_ERR_INVALID_ARG for a null or misaligned pos). */
+ab_status ab_build_packed(ab_ctx* ctx, const ab_domain* dom, int64_t n,
+                          const float* pos);
+
 /* Shape of the last cell list: cells per axis (host int32[3]), the total
  * (host int64), and the stencil reach per axis (host int32[3]: the box
  * search visits cells c - reach .. c + reach).  Along x the cells may be a
@@ -221,6 +230,13 @@ ab_status ab_pair_sum_bwd(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
  * AB_ERR_CUDA. */
 ab_status ab_pair_energy_grad(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
                               float* E, float* grad_pos4, double* energy);
+
+/* ab_pair_energy_grad with the gradient packed as dim floats per particle:
+ * grad_pos (device float32[n][dim], optional, 4-byte aligned), the same
+ * values as the first dim components of grad_pos4.  Errors as
+ * ab_pair_energy_grad. */
+ab_status ab_pair_energy_grad_packed(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
+                                     float* E, float* grad_pos, double* energy);
 
 /* Export the neighbour relation of the last cell list as CSR in the
  * caller's particle order: offsets (device int64[n+1]) and idx (device

@@ -95,6 +95,7 @@ class Context:
         _check(_lib.ab_create(ctypes.byref(h), int(device), ctypes.c_void_p(s)))
         self.handle = h
         self.n = 0
+        self.dim = 0
         self.build_seq = 0
 
     def _stream(self):
@@ -125,11 +126,18 @@ def ab_sync(ctx: Context):
 
 
 def ab_build(ctx: Context, dom: _abi.ab_domain, pos4: torch.Tensor):
-    """Cell-list build (hash, scan, stable scatter) of ``pos4`` float32[n,4]."""
-    pos4 = _dev(pos4, torch.float32, (4,), "pos4")
-    ctx._stream()
-    _check(_lib.ab_build(ctx.handle, ctypes.byref(dom), pos4.shape[0], _ptr(pos4)), ctx)
+    """Cell-list build (hash, scan, stable scatter) of ``pos4`` float32[n,4],
+    or of positions packed as float32[n,dim] (``ab_build_packed``)."""
+    if pos4.dim() == 2 and pos4.shape[1] == dom.dim:
+        pos = _dev(pos4, torch.float32, (dom.dim,), "pos")
+        ctx._stream()
+        _check(_lib.ab_build_packed(ctx.handle, ctypes.byref(dom), pos.shape[0], _ptr(pos)), ctx)
+    else:
+        pos4 = _dev(pos4, torch.float32, (4,), "pos4")
+        ctx._stream()
+        _check(_lib.ab_build(ctx.handle, ctypes.byref(dom), pos4.shape[0], _ptr(pos4)), ctx)
     ctx.n = pos4.shape[0]
+    ctx.dim = dom.dim
     ctx.build_seq += 1
     return ctx.build_seq
 
@@ -201,6 +209,24 @@ def ab_pair_energy_grad(ctx: Context, op, params, E=None, grad_pos4=None, energy
     _check(_lib.ab_pair_energy_grad(ctx.handle, op, ctypes.byref(params), _ptr(E), _ptr(grad_pos4),
                                     _ptr(energy)), ctx)
     return E, grad_pos4, energy
+
+
+def ab_pair_energy_grad_packed(ctx: Context, op, params, E=None, grad_pos=None, energy=None):
+    """ab_pair_energy_grad with the gradient as float32[n, dim]."""
+    op = OPS.get(op, op)
+    if E is None:
+        E = torch.empty(ctx.n, dtype=torch.float32, device=ctx.device)
+    if grad_pos is None:
+        grad_pos = torch.empty((ctx.n, ctx.dim), dtype=torch.float32, device=ctx.device)
+    if energy is None:
+        energy = torch.empty((), dtype=torch.float64, device=ctx.device)
+    _dev(E, torch.float32, None, "E")
+    _dev(grad_pos, torch.float32, (ctx.dim,), "grad_pos")
+    _dev(energy, torch.float64, None, "energy")
+    ctx._stream()
+    _check(_lib.ab_pair_energy_grad_packed(ctx.handle, op, ctypes.byref(params), _ptr(E),
+                                           _ptr(grad_pos), _ptr(energy)), ctx)
+    return E, grad_pos, energy
 
 
 def ab_pair_list(ctx: Context, cap: int | None = None):

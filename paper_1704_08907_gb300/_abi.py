@@ -52,6 +52,7 @@ SIGNATURES = {
     "ab_set_stream": (ST, [P, P]),
     "ab_sync": (ST, [P]),
     "ab_build": (ST, [P, ctypes.POINTER(ab_domain), I64, P]),
+    "ab_build_packed": (ST, [P, ctypes.POINTER(ab_domain), I64, P]),
     "ab_cell_shape": (ST, [P, P, P, P]),
     "ab_cell_export": (ST, [P, P, P]),
     "ab_pair_sum": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P]),
@@ -63,6 +64,7 @@ SIGNATURES = {
                                   P, P, P, P]),
     "ab_bd_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, F32, F32, U64, U64]),
     "ab_pair_energy_grad": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P]),
+    "ab_pair_energy_grad_packed": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P]),
     "ab_md_step": (ST, [P, ctypes.POINTER(ab_domain), I64, P, P, P, F32]),
     "ab_kernel_solve": (ST, [P, I64, P, I32, P, F32, F32, I32, F32, I32, P,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),

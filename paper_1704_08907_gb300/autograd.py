@@ -8,7 +8,8 @@ from __future__ import annotations
 import torch
 
 from . import (AB_OP_GAUSS, AB_OP_LJ, Context, OpParams, ab_build, ab_kernel_matvec,
-               ab_kernel_matvec_bwd, ab_pair_energy_grad, ab_pair_sum, ab_pair_sum_bwd)
+               ab_kernel_matvec_bwd, ab_pair_energy_grad, ab_pair_energy_grad_packed,
+               ab_pair_sum, ab_pair_sum_bwd)
 
 
 def _ensure_built(abctx: Context, dom, pos4, seq):
@@ -97,12 +98,14 @@ def lj_energy_forces(abctx: Context, dom, pos4: torch.Tensor, eps: float, sigma:
                      E=None, F=None, energy=None, g=None):
     """One rebuild + LJ energy forward + adjoint (forces = -dE/dx).
 
-    Returns (E per particle, minus-force dE/dx as float32[n,4], total energy
-    float64 scalar tensor).  Buffers may be passed in to avoid allocation.
-    With g None (the loss is the total energy) the energy and its gradient
-    come from one fused walk; with an explicit upstream g the forward and the
-    adjoint run separately."""
+    Positions are float32[n,4] or packed float32[n,dim]; the gradient comes
+    back in the same layout.  Returns (E per particle, minus-force dE/dx,
+    total energy float64 scalar tensor).  Buffers may be passed in to avoid
+    allocation.  With g None (the loss is the total energy) the energy and
+    its gradient come from one fused walk; with an explicit upstream g the
+    forward and the adjoint run separately."""
     n = pos4.shape[0]
+    packed = pos4.shape[1] == dom.dim
     ab_build(abctx, dom, pos4)
     prm = OpParams(eps=eps, sigma=sigma)
     if energy is None:
@@ -112,8 +115,16 @@ def lj_energy_forces(abctx: Context, dom, pos4: torch.Tensor, eps: float, sigma:
     if g is None:
         if E is None:
             E = torch.empty(n, dtype=torch.float32, device=pos4.device)
-        ab_pair_energy_grad(abctx, AB_OP_LJ, prm, E=E, grad_pos4=F, energy=energy)
+        if packed:
+            ab_pair_energy_grad_packed(abctx, AB_OP_LJ, prm, E=E, grad_pos=F, energy=energy)
+        else:
+            ab_pair_energy_grad(abctx, AB_OP_LJ, prm, E=E, grad_pos4=F, energy=energy)
         return E, F, energy
     E = ab_pair_sum(abctx, AB_OP_LJ, prm, out=E, energy=energy)
-    ab_pair_sum_bwd(abctx, AB_OP_LJ, prm, None, g, grad_pos4=F)
+    if packed:
+        G4 = torch.empty((n, 4), dtype=torch.float32, device=pos4.device)
+        ab_pair_sum_bwd(abctx, AB_OP_LJ, prm, None, g, grad_pos4=G4)
+        F.copy_(G4[:, :dom.dim])
+    else:
+        ab_pair_sum_bwd(abctx, AB_OP_LJ, prm, None, g, grad_pos4=F)
     return E, F, energy

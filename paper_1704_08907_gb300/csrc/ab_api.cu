@@ -275,13 +275,16 @@ ab_status ab_sync(ab_ctx* c) {
     return AB_OK;
 }
 
-ab_status ab_build(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos4) {
+static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos,
+                            bool packed) {
     if (!c) return AB_ERR_INVALID_ARG;
     ab_status s = check_domain(c, dom);
     if (s != AB_OK) return s;
     if (n < 0 || n >= (int64_t(1) << 31) - 1) return fail(c, AB_ERR_INVALID_ARG, "n out of range");
-    if (n > 0 && (!pos4 || !aligned16(pos4)))
+    if (!packed && n > 0 && (!pos || !aligned16(pos)))
         return fail(c, AB_ERR_INVALID_ARG, "pos4 must be a 16-byte aligned device pointer");
+    if (packed && n > 0 && (!pos || ((uintptr_t)pos & 3)))
+        return fail(c, AB_ERR_INVALID_ARG, "pos must be a 4-byte aligned device pointer");
     cudaSetDevice(c->device);
     CellList& cl = c->cl;
     cl.valid = false;
@@ -317,11 +320,19 @@ ab_status ab_build(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos4
     if (s != AB_OK) return s;
     cl.n = n;
     cl.g = g;
-    e = ab::launch_build(cl, (const float4*)pos4, c->sc, c->d_err, c->stream);
+    e = ab::launch_build(cl, pos, packed, c->sc, c->d_err, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_build launch");
-    cl.user_pos = pos4;
+    cl.user_pos = pos;
     cl.valid = true;
     return AB_OK;
+}
+
+ab_status ab_build(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos4) {
+    return build_impl(c, dom, n, pos4, false);
+}
+
+ab_status ab_build_packed(ab_ctx* c, const ab_domain* dom, int64_t n, const float* pos) {
+    return build_impl(c, dom, n, pos, true);
 }
 
 ab_status ab_cell_shape(ab_ctx* c, int32_t* ncell, int64_t* n_cells, int32_t* reach) {
@@ -403,23 +414,27 @@ ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float*
     return AB_OK;
 }
 
-ab_status ab_pair_energy_grad(ab_ctx* c, ab_op op, const ab_op_params* prm, float* E,
-                              float* grad_pos4, double* energy) {
+static ab_status energy_grad_impl(ab_ctx* c, ab_op op, const ab_op_params* prm, float* E,
+                                  float* grad, bool packed, double* energy) {
     if (!c) return AB_ERR_INVALID_ARG;
     ab_status s = require_cells(c);
     if (s != AB_OK) return s;
     if (op != AB_OP_LJ) return fail(c, AB_ERR_UNSUPPORTED, "energy + gradient fused for LJ only");
     if (!prm) return fail(c, AB_ERR_INVALID_ARG, "params is NULL");
     const int64_t n = c->cl.n;
-    if (grad_pos4 && !aligned16(grad_pos4))
+    if (!packed && grad && !aligned16(grad))
         return fail(c, AB_ERR_INVALID_ARG, "grad_pos4 must be 16-byte aligned");
-    if (overlaps(E, (size_t)n * 4, grad_pos4, (size_t)n * 16) ||
-        overlaps(energy, 8, E, (size_t)n * 4) || overlaps(energy, 8, grad_pos4, (size_t)n * 16))
+    if (packed && grad && ((uintptr_t)grad & 3))
+        return fail(c, AB_ERR_INVALID_ARG, "grad_pos must be 4-byte aligned");
+    const size_t gbytes = (size_t)n * (packed ? 4 * (size_t)c->cl.g.dim : 16);
+    if (overlaps(E, (size_t)n * 4, grad, gbytes) ||
+        overlaps(energy, 8, E, (size_t)n * 4) || overlaps(energy, 8, grad, gbytes))
         return fail(c, AB_ERR_ALIAS, "outputs overlap");
     cudaSetDevice(c->device);
     ab::PairOut o;
     o.out = E;
-    o.grad_pos = (float4*)grad_pos4;
+    if (packed) o.grad_packed = grad;
+    else o.grad_pos = (float4*)grad;
     const int grid = ab::pair_grid(n);
     if (energy) {
         if ((s = ensure_partial(c, (size_t)grid)) != AB_OK) return s;
@@ -434,6 +449,16 @@ ab_status ab_pair_energy_grad(ab_ctx* c, ab_op op, const ab_op_params* prm, floa
         if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_energy_grad energy");
     }
     return AB_OK;
+}
+
+ab_status ab_pair_energy_grad(ab_ctx* c, ab_op op, const ab_op_params* prm, float* E,
+                              float* grad_pos4, double* energy) {
+    return energy_grad_impl(c, op, prm, E, grad_pos4, false, energy);
+}
+
+ab_status ab_pair_energy_grad_packed(ab_ctx* c, ab_op op, const ab_op_params* prm, float* E,
+                                     float* grad_pos, double* energy) {
+    return energy_grad_impl(c, op, prm, E, grad_pos, true, energy);
 }
 
 ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,

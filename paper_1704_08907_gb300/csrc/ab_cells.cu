@@ -29,18 +29,27 @@ inline int ew_grid(int64_t n) {
     return b < 1 ? 1 : (int)b;
 }
 
+// Position i of the caller's array: float4 (x, y, z, pad) records, or
+// PACKED records of DIM floats (x, y[, z]).
+template <int DIM, bool PACKED>
+__device__ __forceinline__ float4 load_pos(const float* __restrict__ pos, int64_t i) {
+    if (!PACKED) return __ldg(reinterpret_cast<const float4*>(pos) + i);
+    const float* q = pos + i * DIM;
+    return make_float4(__ldg(q), __ldg(q + 1), DIM == 3 ? __ldg(q + 2) : 0.0f, 0.0f);
+}
+
 // ---------------------------------------------------------------------------
 // (a1) cell hash + histogram.  The atomic's return value is the particle's
 // arrival rank inside its cell (order not deterministic; fixed up below).
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kThreads)
-k_hash(const float4* __restrict__ pos, int64_t n, Geom g,
+k_hash(const float* __restrict__ pos, int64_t n, Geom g,
        uint32_t* __restrict__ cell_id, uint32_t* __restrict__ rank,
        uint32_t* __restrict__ count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float4 p = __ldg(pos + i);
+        float4 p = load_pos<DIM, PACKED>(pos, i);
         uint32_t c = (uint32_t)cell_coord(p.x, g.lo[0], g.inv_w[0], g.n[0]);
         uint32_t cy = (uint32_t)cell_coord(p.y, g.lo[1], g.inv_w[1], g.n[1]);
         c += (uint32_t)g.n[0] * cy;
@@ -68,9 +77,9 @@ k_scatter(int64_t n, const uint32_t* __restrict__ cell_id,
 // (a3) make the sort stable: the final slot of particle p inside its cell is
 // the number of cell members with a smaller original index.  Then gather the
 // position into sorted order.
-template <int DIM>
+template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kThreads)
-k_finalize(int64_t n, const float4* __restrict__ pos,
+k_finalize(int64_t n, const float* __restrict__ pos,
            const uint32_t* __restrict__ cell_id,
            const uint32_t* __restrict__ cell_start,
            const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm,
@@ -84,7 +93,7 @@ k_finalize(int64_t n, const float4* __restrict__ pos,
         for (uint32_t t = a; t < b; ++t) r += (__ldg(tmp + t) < p) ? 1u : 0u;
         uint32_t d = a + r;
         perm[d] = p;
-        float4 q = __ldg(pos + p);
+        float4 q = load_pos<DIM, PACKED>(pos, p);
         spos[d] = make_float4(q.x, q.y, DIM == 3 ? q.z : 0.0f, 0.0f);
     }
 }
@@ -320,17 +329,21 @@ cudaError_t launch_reduce_partials(const double* partial, int count, double* out
     return cudaGetLastError();
 }
 
-cudaError_t launch_build(CellList& cl, const float4* pos, Scratch& sc,
+cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
                          uint32_t* err, cudaStream_t st) {
     const int64_t n = cl.n;
     const int64_t nc = cl.g.n_cells;
     cudaError_t e = cudaMemsetAsync(cl.cell_start, 0, (size_t)(nc + 1) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        if (cl.g.dim == 3)
-            k_hash<3><<<ew_grid(n), kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
-        else
-            k_hash<2><<<ew_grid(n), kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+        const int gr = ew_grid(n);
+        if (cl.g.dim == 3) {
+            if (packed) k_hash<3, true><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+            else k_hash<3, false><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+        } else {
+            if (packed) k_hash<2, true><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+            else k_hash<2, false><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // counts -> offsets in place; entry nc is 0 so cell_start[nc] = n.
@@ -340,10 +353,14 @@ cudaError_t launch_build(CellList& cl, const float4* pos, Scratch& sc,
     if (n > 0) {
         k_scatter<<<ew_grid(n), kThreads, 0, st>>>(n, cl.cell_id, cl.rank, cl.cell_start, cl.tmp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (cl.g.dim == 3)
-            k_finalize<3><<<ew_grid(n), kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
-        else
-            k_finalize<2><<<ew_grid(n), kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+        const int gr = ew_grid(n);
+        if (cl.g.dim == 3) {
+            if (packed) k_finalize<3, true><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+            else k_finalize<3, false><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+        } else {
+            if (packed) k_finalize<2, true><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+            else k_finalize<2, false><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -79,7 +79,7 @@ struct Scratch {
 // ---- launchers (defined in the .cu files) ----------------------------------
 
 // ab_cells.cu
-AB_HIDDEN cudaError_t launch_build(CellList& cl, const float4* pos, Scratch& sc,
+AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
                                    uint32_t* err, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_vars(const CellList& cl, const float* w,
                                          const float* g, float2* sv,
@@ -107,6 +107,7 @@ struct PairOut {
     float* out = nullptr;        // scalar output (user order)
     float4* out4 = nullptr;      // vector output (user order)
     float4* grad_pos = nullptr;  // bwd
+    float* grad_packed = nullptr;  // bwd, dim floats per particle (energy + gradient only)
     float* grad_w = nullptr;     // bwd
     double* partial = nullptr;   // per-block partials (energy or ds)
     int partial_count = 0;

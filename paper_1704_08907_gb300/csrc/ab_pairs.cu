@@ -451,6 +451,12 @@ k_pair_lj_eg(PairParams P, PairOut o) {
         if (o.out) o.out[p] = e;
         if (o.grad_pos)
             o.grad_pos[p] = make_float4(P.eps * gx, P.eps * gy, DIM == 3 ? P.eps * gz : 0.0f, 0.0f);
+        if (o.grad_packed) {   // DIM floats per particle
+            float* q = o.grad_packed + (int64_t)p * DIM;
+            q[0] = P.eps * gx;
+            q[1] = P.eps * gy;
+            if (DIM == 3) q[2] = P.eps * gz;
+        }
     }
     if (o.partial) block_partial<kPairThreads>(live ? (double)e : 0.0, o.partial);
 }

@@ -78,3 +78,49 @@ def test_fused_errors(ab, ctx):
         ab.ab_pair_energy_grad(ctx, "lj", ab.OpParams(), E=buf.view(-1)[:1000], grad_pos4=buf)
     assert e.value.status == ab._abi.AB_ERR_ALIAS
     ab.ab_sync(ctx)
+
+
+@pytest.mark.parametrize("case", ["c2", "2d"])
+def test_packed_layout_equals_pos4(ab, ctx, case):
+    """Positions packed as dim floats per particle (ab_build_packed) and the
+    packed gradient give bit for bit the pos4 results: the same cell list,
+    energies, gradients and total energy."""
+    if case == "c2":
+        w = synth.c2()
+        dim, periodic, r, pos = 3, w.periodic, w.radius, w.pos
+    else:
+        dim, periodic, r = 2, (1, 0), 0.02
+        pos = synth.uniform_positions(200000, 2, 7)
+    prm = ab.OpParams(eps=1.0, sigma=0.01)
+    dom = ab.Domain(dim, periodic, r)
+    ab.ab_build(ctx, dom, dev(pos))
+    perm4, start4 = ab.ab_cell_export(ctx)
+    E4, G4, e4 = ab.ab_pair_energy_grad(ctx, "lj", prm)
+    packed = dev(np.ascontiguousarray(pos[:, :dim]))
+    ab.ab_build(ctx, dom, packed)
+    perm, start = ab.ab_cell_export(ctx)
+    E, G, e = ab.ab_pair_energy_grad_packed(ctx, "lj", prm)
+    ab.ab_sync(ctx)
+    assert G.shape == (pos.shape[0], dim)
+    assert torch.equal(perm, perm4) and torch.equal(start, start4)
+    assert torch.equal(E, E4) and torch.equal(e, e4)
+    assert torch.equal(G, G4[:, :dim])
+
+
+def test_packed_wrapper_and_errors(ab, ctx):
+    from paper_1704_08907_gb300.autograd import lj_energy_forces
+    w = synth.c2(n=1 << 16)
+    dom = ab.Domain(3, w.periodic, w.radius)
+    E4, F4, e4 = lj_energy_forces(ctx, dom, dev(w.pos), 1.0, 0.01)
+    E, F, e = lj_energy_forces(ctx, dom, dev(np.ascontiguousarray(w.pos[:, :3])), 1.0, 0.01)
+    assert F.shape == (w.n, 3) and torch.equal(F, F4[:, :3]) and torch.equal(e, e4)
+    g = torch.rand(w.n, dtype=torch.float32, device="cuda:0")
+    _, Fg4, _ = lj_energy_forces(ctx, dom, dev(w.pos), 1.0, 0.01, g=g)
+    _, Fg, _ = lj_energy_forces(ctx, dom, dev(np.ascontiguousarray(w.pos[:, :3])), 1.0, 0.01, g=g)
+    assert torch.equal(Fg, Fg4[:, :3])
+    buf = torch.empty(w.n * 3, dtype=torch.float32, device="cuda:0")
+    with pytest.raises(ab.AbError) as err:   # E overlapping the packed gradient
+        ab.ab_pair_energy_grad_packed(ctx, "lj", ab.OpParams(eps=1.0, sigma=0.01),
+                                      E=buf[: w.n], grad_pos=buf.view(w.n, 3))
+    assert err.value.status == ab._abi.AB_ERR_ALIAS
+    ab.ab_sync(ctx)
