@@ -1171,13 +1171,12 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     const int split = (mblocks < 4 * (int64_t)g_num_sms && tiles >= 2) ? 2 : 1;
     if (split == 2 && (e = cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st)) != cudaSuccess)
         return e;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_dense_tc_fwd<TF32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set on every launch: the attribute belongs to the current device, and
+    // contexts on several devices may share this process (a microsecond
+    // against a kernel of milliseconds)
+    e = cudaFuncSetAttribute(k_dense_tc_fwd<TF32, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes);
+    if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)mblocks, (unsigned)split);
     k_dense_tc_fwd<TF32, SPLIT><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg,
                                                                       sl2e, out, err);
@@ -1227,25 +1226,17 @@ cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* X, const f
         return e;
     const dim3 grid((unsigned)mb, (unsigned)split);
     if (prec == AB_PREC_BF16 || prec == AB_PREC_TF32) {
-        static bool attr = false;
-        if (!attr) {
-            if ((e = cudaFuncSetAttribute(k_dense_tc_gradx<false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kGradSmemBytes)) != cudaSuccess)
-                return e;
-            attr = true;
-        }
+        if ((e = cudaFuncSetAttribute(k_dense_tc_gradx<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kGradSmemBytes)) != cudaSuccess)
+            return e;   // per device: set on every launch
         k_dense_tc_gradx<false><<<grid, kThreadsTC, kGradSmemBytes, st>>>(m, nb, X, Yt, centre, gimg,
                                                                           wimg, sl2e, s, dX, partial, err);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            if ((e = cudaFuncSetAttribute(k_dense_tc_gradx<true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kGradSmemBytes)) != cudaSuccess)
-                return e;
-            attr = true;
-        }
+        if ((e = cudaFuncSetAttribute(k_dense_tc_gradx<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kGradSmemBytes)) != cudaSuccess)
+            return e;   // per device: set on every launch
         k_dense_tc_gradx<true><<<grid, kThreadsTC, kGradSmemBytes, st>>>(m, nb, X, Yt, centre, gimg,
                                                                          wimg, sl2e, s, dX, partial, err);
     }
