@@ -116,3 +116,54 @@ def test_md_step_errors_and_stale(ab, ctx):
         ab.ab_md_step(ctx, dom, pos, vel, acc, float("nan"))
     assert e.value.status == ab._abi.AB_ERR_INVALID_ARG
     ab.ab_sync(ctx)
+
+
+def test_linear_spring_md_step_against_oracle(ab, ctx):
+    """The molecular-dynamics example program of Sec. 1: point particles
+    interacting via a linear spring force, here AB_OP_SOFT (rest length r:
+    f_i = sum_j -k (r - d) dx_ij / d for d < r), advanced by Eqs. 2-3 in 3-D.
+    One step from a seeded moving state against the oracle's force sum and
+    step."""
+    n, r, k, dt = 20000, 0.05, 50.0, 1.0e-3
+    periodic = (1, 1, 1)
+    pos = synth.uniform_positions(n, 3, 21)
+    vel = synth.pack4(np.random.default_rng(22).uniform(-0.05, 0.05, (n, 3)).astype(np.float32))
+    dom = ab.Domain(3, periodic, r)
+    p, v = dev(pos), dev(vel)
+    ab.ab_build(ctx, dom, p)
+    F = ab.ab_pair_sum(ctx, "soft", ab.OpParams(k=k))
+    ab.ab_md_step(ctx, dom, p, v, F, dt)
+    box = oracle.Box(3, periodic, (0, 0, 0), (1, 1, 1), r)
+    off, idx = oracle.CellList(box, pos).neighbours()
+    Fo = oracle.pair_values("soft", box, pos, off, idx, params={"k": k})
+    den = oracle.abs_terms("soft", box, pos, off, idx, params={"k": k})
+    po, vo = md.md_step(pos, vel, Fo, 3, periodic, (0, 0, 0), (1, 1, 1), dt)
+    vh, ph = host(v)[:, :3].astype(np.float64), host(p)[:, :3]
+    # the pair-sum bar on dt * F plus FP32 roundings of v, dt * F and their sum
+    tol_v = dt * 1e-5 * np.maximum(np.abs(Fo[:, :3]), den[:, :3]) + 2.0 ** -22 * (
+        np.abs(vo[:, :3]) + np.abs(vel[:, :3]) + dt * np.abs(Fo[:, :3]))
+    assert np.all(np.abs(vh - vo[:, :3]) <= tol_v + 1e-12)
+    # position: dt times that, plus two FP32 roundings of a coordinate in [0, 1)
+    assert np.all(_pdiff(ph, po[:, :3], periodic) <= dt * tol_v + 2.4e-7)
+    assert np.abs(vh - vel[:, :3]).max() > 0   # the springs did act
+
+
+def test_linear_spring_time_loop_conserves_momentum(ab, ctx):
+    """20 steps of the linear-spring loop from rest: the spring force is
+    antisymmetric pair by pair, so the total momentum stays 0 up to FP32
+    rounding of the per-particle sums and updates."""
+    n, r, k, dt = 50000, 0.04, 50.0, 1.0e-3
+    dom = ab.Domain(3, (1, 1, 1), r)
+    pos = dev(synth.uniform_positions(n, 3, 23))
+    vel = torch.zeros((n, 4), dtype=torch.float32, device="cuda:0")
+    prm = ab.OpParams(k=k)
+    bound = 0.0
+    for _ in range(20):
+        ab.ab_build(ctx, dom, pos)
+        F = ab.ab_pair_sum(ctx, "soft", prm)
+        bound += dt * float(F[:, :3].abs().double().sum()) * 2.0 ** -22
+        ab.ab_md_step(ctx, dom, pos, vel, F, dt)
+    ab.ab_sync(ctx)
+    v = host(vel)[:, :3].astype(np.float64)
+    assert np.abs(v.sum(axis=0)).max() <= bound + np.abs(v).sum() * 2.0 ** -22
+    assert np.abs(v).max() > 0
