@@ -295,7 +295,7 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
         // all per-particle buffers share one capacity
         const size_t want = nn + nn / 4 + 64;
         void* fresh[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t bytes[5] = {16, 4, 4, 4, 4};
+        const size_t bytes[5] = {16, 4, 4, 4, 8};   // tmp: (original index, cell) pairs
         for (int t = 0; t < 5; ++t) {
             e = cudaMallocAsync(&fresh[t], want * bytes[t], c->stream);
             if (e != cudaSuccess) {

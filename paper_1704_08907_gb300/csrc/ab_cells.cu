@@ -62,15 +62,15 @@ k_hash(const float* __restrict__ pos, int64_t n, Geom g,
     }
 }
 
-// (a3) scatter original indices into their (unordered) slot.
+// (a3) scatter (original index, cell) into the particle's (unordered) slot.
 __global__ void __launch_bounds__(kThreads)
 k_scatter(int64_t n, const uint32_t* __restrict__ cell_id,
           const uint32_t* __restrict__ rank,
-          const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ tmp) {
+          const uint32_t* __restrict__ cell_start, uint2* __restrict__ tmp) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t c = cell_id[i];
-        tmp[cell_start[c] + rank[i]] = (uint32_t)i;
+        tmp[cell_start[c] + rank[i]] = make_uint2((uint32_t)i, c);
     }
 }
 
@@ -80,17 +80,18 @@ k_scatter(int64_t n, const uint32_t* __restrict__ cell_id,
 template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kThreads)
 k_finalize(int64_t n, const float* __restrict__ pos,
-           const uint32_t* __restrict__ cell_id,
            const uint32_t* __restrict__ cell_start,
-           const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm,
+           const uint2* __restrict__ tmp, uint32_t* __restrict__ perm,
            float4* __restrict__ spos) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t p = tmp[s];
-        uint32_t c = cell_id[p];
+        // the slot carries its cell, so the cell range and the position are
+        // fetched side by side
+        const uint2 pc = tmp[s];
+        const uint32_t p = pc.x, c = pc.y;
         uint32_t a = cell_start[c], b = cell_start[c + 1];
         uint32_t r = 0;
-        for (uint32_t t = a; t < b; ++t) r += (__ldg(tmp + t) < p) ? 1u : 0u;
+        for (uint32_t t = a; t < b; ++t) r += (__ldg(&tmp[t].x) < p) ? 1u : 0u;
         uint32_t d = a + r;
         perm[d] = p;
         float4 q = load_pos<DIM, PACKED>(pos, p);
@@ -351,15 +352,16 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
                         sc.scan_ticket, err, -1, 0, st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        k_scatter<<<ew_grid(n), kThreads, 0, st>>>(n, cl.cell_id, cl.rank, cl.cell_start, cl.tmp);
+        uint2* tmp = reinterpret_cast<uint2*>(cl.tmp);   // 8 bytes a particle
+        k_scatter<<<ew_grid(n), kThreads, 0, st>>>(n, cl.cell_id, cl.rank, cl.cell_start, tmp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int gr = ew_grid(n);
         if (cl.g.dim == 3) {
-            if (packed) k_finalize<3, true><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
-            else k_finalize<3, false><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+            if (packed) k_finalize<3, true><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_start, tmp, cl.perm, cl.spos);
+            else k_finalize<3, false><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_start, tmp, cl.perm, cl.spos);
         } else {
-            if (packed) k_finalize<2, true><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
-            else k_finalize<2, false><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_id, cl.cell_start, cl.tmp, cl.perm, cl.spos);
+            if (packed) k_finalize<2, true><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_start, tmp, cl.perm, cl.spos);
+            else k_finalize<2, false><<<gr, kThreads, 0, st>>>(n, pos, cl.cell_start, tmp, cl.perm, cl.spos);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
