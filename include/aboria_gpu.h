@@ -136,7 +136,7 @@ ab_status ab_sync(ab_ctx* ctx);
  *   n_k = max(1, floor(L_k / (r (1 + 2^-18) + L_k 2^-18)))
  * (a width a hair above r, so rounding of the FP32 cell index can never hide
  * a pair from the 3^d stencil), coarsened uniformly if the table would
- * exceed max(2^22, 4n) cells; then, room permitting, the x cells are split
+ * exceed max(2^22, 8n) cells; then, room permitting, the x cells are split
  * into kx = 2..4 parts (see ab_cell_shape).  Steps: cell hash + histogram, exclusive scan
  * of the counts (cell offsets), stable counting-sort scatter of the
  * positions.  The sort is stable: within a cell, particles keep ascending

@@ -116,7 +116,7 @@ Geom make_geom(const ab_domain* d, int64_t n) {
         if (c > (double)(1 << 21)) c = (double)(1 << 21);
         nk[k] = (int64_t)c;
     }
-    const int64_t cap = n * 4 > (int64_t(1) << 22) ? n * 4 : (int64_t(1) << 22);
+    const int64_t cap = n * 8 > (int64_t(1) << 22) ? n * 8 : (int64_t(1) << 22);
     for (;;) {
         int64_t t = nk[0] * nk[1] * nk[2];
         if (t <= cap) break;
