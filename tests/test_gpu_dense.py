@@ -177,14 +177,24 @@ def test_tensor_core_adjoint(ab, ctx, prec, m, n):
 
 
 def test_tensor_core_adjoint_full_size_sampled(ab, ctx):
+    """65,536 x 65,536 x 64, BF16X3: sampled rows of dX, sampled points of dY
+    and sampled right-hand-side rows of dW against the FP64 oracle."""
     d = synth.c4()
     m, n = d.X.shape[0], d.Y.shape[0]
+    dW = torch.empty((n, 64), dtype=torch.float32, device="cuda:0")
     dX = torch.empty((m, 4), dtype=torch.float32, device="cuda:0")
+    dY = torch.empty((n, 4), dtype=torch.float32, device="cuda:0")
     ds = torch.empty((), dtype=torch.float64, device="cuda:0")
     ab.ab_kernel_matvec_bwd(ctx, _dev4(d.X), _dev4(d.Y), dev(d.W), d.s, "bf16x3", dev(d.G),
-                            None, dX, None, ds)
+                            dW, dX, dY, ds)
     ab.ab_sync(ctx)
     rows = synth.query_sample(m, 64, 10)
     rX = dense.grad_X(d.X, d.Y, d.W, d.G, d.s, rows=rows)
     assert np.max(np.abs(host(dX)[rows, :3] - rX)) <= 1e-4 * np.abs(rX).max()
+    cols = synth.query_sample(n, 64, 11)
+    rY = dense.grad_Y(d.X, d.Y, d.W, d.G, d.s, cols=cols)
+    assert np.max(np.abs(host(dY)[cols, :3] - rY)) <= 1e-4 * np.abs(rY).max()
+    rW = dense.grad_W(d.X, d.Y, d.G, d.s, cols=cols)
+    aW = dense.grad_W(d.X, d.Y, np.abs(d.G), d.s, cols=cols)
+    assert np.max(np.abs(host(dW)[cols] - rW) / aW) <= TC_TOL
     assert np.isfinite(float(ds))
