@@ -348,9 +348,14 @@ k_pair_fwd_q(PairParams P, PairOut o) {
                     const float inv_d = rsqrt_approx(d2);
                     mag = -P.c * ex2_approx(-kLog2e * (d2 * inv_d)) * inv_d;
                 } else {
-                    // r - d cancels near the cut-off: take d correctly rounded
-                    const float d = __fsqrt_rn(d2);
-                    mag = __fdiv_rn(-P.k * (P.r - d), d);
+                    // -k (r - d) / d with r - d = (r^2 - d^2) / (r + d): the
+                    // fma rounds r^2 - d^2 once, so the term keeps its relative
+                    // accuracy up to the cut-off, where r - d cancels, and d
+                    // enters only through 1/d and r + d (approximate
+                    // reciprocals, a few ulp)
+                    const float inv_d = rsqrt_approx(d2);
+                    const float d = d2 * inv_d;
+                    mag = (-P.k * fmaf(P.r, P.r, -d2)) * (inv_d * rcp_approx(P.r + d));
                 }
                 a0 = fmaf(mag, dx, a0);
                 a1 = fmaf(mag, dy, a1);
