@@ -80,17 +80,21 @@ def test_fused_errors(ab, ctx):
     ab.ab_sync(ctx)
 
 
-@pytest.mark.parametrize("case", ["c2", "2d"])
+@pytest.mark.parametrize("case", ["c2", "2d", "general"])
 def test_packed_layout_equals_pos4(ab, ctx, case):
     """Positions packed as dim floats per particle (ab_build_packed) and the
     packed gradient give bit for bit the pos4 results: the same cell list,
-    energies, gradients and total energy."""
+    energies, gradients and total energy (fast path, 2-D with a wall, and
+    the general path of a periodic axis with fewer than 5 cells)."""
     if case == "c2":
         w = synth.c2()
         dim, periodic, r, pos = 3, w.periodic, w.radius, w.pos
-    else:
+    elif case == "2d":
         dim, periodic, r = 2, (1, 0), 0.02
         pos = synth.uniform_positions(200000, 2, 7)
+    else:
+        dim, periodic, r = 3, (1, 1, 1), 0.26
+        pos = synth.uniform_positions(20000, 3, 8)
     prm = ab.OpParams(eps=1.0, sigma=0.01)
     dom = ab.Domain(dim, periodic, r)
     ab.ab_build(ctx, dom, dev(pos))
