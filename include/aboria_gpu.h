@@ -21,8 +21,9 @@
  *    or retains them past the call, except that ab_build records the
  *    positions pointer and size to detect stale use.
  *  - Positions are float32[n][4] (x, y, z, pad), 16-byte aligned; for d = 2
- *    the z and pad components are ignored.  Per-particle scalars are
- *    float32[n].  Inputs and outputs are in the caller's particle order.
+ *    the z and pad components are ignored.  The *_packed entry points take
+ *    d floats per particle instead (4-byte aligned).  Per-particle scalars
+ *    are float32[n].  Inputs and outputs are in the caller's particle order.
  *  - Every call is asynchronous on the context's CUDA stream.  Argument
  *    errors are returned immediately and launch nothing.  Errors detected on
  *    the device (a wait that timed out) are latched and returned by the next
