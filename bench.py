@@ -401,6 +401,15 @@ def also_dense(reps=5):
             float((outs[prec].double() - ref).abs().max().item() / scale)
     res["speedup_bf16x3_vs_fp32"] = res["fp32"]["ms"] / res["bf16x3"]["ms"]
     res["speedup_tf32x3_vs_fp32"] = res["fp32"]["ms"] / res["tf32x3"]["ms"]
+    # the BF16X3 forward against the measured bf16 tensor peak: algorithmic
+    # tensor work = 3 bf16 products of 2 M N nrhs (P_hi W_hi, P_hi W_lo,
+    # P_lo W_hi); the kernel also issues P_lo W_lo, which only adds accuracy
+    pk, pk_kind = peaks()
+    tc_tf = 3.0 * 2.0 * m * n * nrhs / (res["bf16x3"]["ms"] * 1e-3) / 1e12
+    res["roofline_bf16x3"] = {"bound": "tensor", "achieved": tc_tf, "peak": pk["bf16_tflops"],
+                              "unit": "TFLOP/s", "frac": tc_tf / pk["bf16_tflops"],
+                              "peak_kind": pk_kind + " bf16 burst",
+                              "exps_per_s": m * n / (res["bf16x3"]["ms"] * 1e-3)}
     # adjoint: dW, dX, dY and ds (lengthscale) in one call
     G = torch.from_numpy(d.G).to(dev)
     dW = torch.empty_like(W)
