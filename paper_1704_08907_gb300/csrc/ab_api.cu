@@ -388,11 +388,12 @@ ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float*
         return fail(c, AB_ERR_ALIAS, "output overlaps an input");
     cudaSetDevice(c->device);
     cudaError_t e;
-    if (uses_w) {
+    if (op == AB_OP_SPH_FORCE) {
         if ((s = ensure_sv(c, n)) != AB_OK) return s;
-        e = op == AB_OP_SPH_FORCE
-                ? ab::launch_gather_pairs(c->cl, (const float2*)w, c->sc.sv, c->stream)
-                : ab::launch_gather_vars(c->cl, w, nullptr, c->sc.sv, c->stream);
+        e = ab::launch_gather_pairs(c->cl, (const float2*)w, c->sc.sv, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum gather");
+    } else if (uses_w) {   // w rides in the pad component of the sorted positions
+        e = ab::launch_gather_w_pos(c->cl, w, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum gather");
     }
     ab::PairOut o;

@@ -110,6 +110,17 @@ k_gather_vars(int64_t n, const uint32_t* __restrict__ perm,
     }
 }
 
+// The per-particle weight w, in sorted order, into the pad component of the
+// sorted positions: a forward that needs only w (Gaussian sum, SPH density)
+// then reads it with the candidate's position, no separate load.
+__global__ void __launch_bounds__(kThreads)
+k_gather_w_pos(int64_t n, const uint32_t* __restrict__ perm, const float* __restrict__ w,
+               float4* __restrict__ spos) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        spos[s].w = __ldg(w + perm[s]);
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_gather_pairs(int64_t n, const uint32_t* __restrict__ perm, const float2* __restrict__ wv,
                float2* __restrict__ sv) {
@@ -372,6 +383,12 @@ cudaError_t launch_gather_vars(const CellList& cl, const float* w, const float* 
                                float2* sv, cudaStream_t st) {
     if (cl.n <= 0) return cudaSuccess;
     k_gather_vars<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, w, g, sv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st) {
+    if (cl.n <= 0) return cudaSuccess;
+    k_gather_w_pos<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, w, cl.spos);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ struct Scratch {
 // ab_cells.cu
 AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
                                    uint32_t* err, cudaStream_t st);
+AB_HIDDEN cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_vars(const CellList& cl, const float* w,
                                          const float* g, float2* sv,
                                          cudaStream_t st);

@@ -293,7 +293,9 @@ __device__ __forceinline__ void block_partial(double v, double* partial) {
     }
 }
 
-// Forward for the cheap operators (COUNT, GAUSS): direct visit.
+// Forward for the cheap operators (COUNT, GAUSS, SPH density): direct visit.
+// The weight w_j (GAUSS) or mass m_j (SPH) comes in the pad component of the
+// sorted position, loaded with the candidate.
 template <int DIM, bool GENERAL, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd(PairParams P, PairOut o) {
@@ -302,19 +304,19 @@ k_pair_fwd(PairParams P, PairOut o) {
     const float4 pi = __ldg(P.spos + s);
     float a0 = 0.0f;
     visit_pairs<DIM, GENERAL>(P, s, pi,
-        [&](uint32_t j, const float4&, float, float, float, float d2) {
+        [&](uint32_t, const float4& pj, float, float, float, float d2) {
             if (OP == AB_OP_COUNT) {
                 a0 += 1.0f;
             } else if (OP == AB_OP_GAUSS) {
-                a0 += __ldg(&P.sv[j].x) * ex2_approx(-P.s_log2e * d2);
+                a0 += pj.w * ex2_approx(-P.s_log2e * d2);
             } else {   // SPH_DENSITY: m_j W(d)
                 float q;
                 const float t = wend_t(d2, P.inv_r, q);
                 const float t2 = t * t;
-                a0 = fmaf(__ldg(&P.sv[j].x) * P.wend_a, t2 * t2 * fmaf(4.0f, q, 1.0f), a0);
+                a0 = fmaf(pj.w * P.wend_a, t2 * t2 * fmaf(4.0f, q, 1.0f), a0);
             }
         });
-    if (OP == AB_OP_SPH_DENSITY) a0 = fmaf(__ldg(&P.sv[s].x), P.wend_a, a0);   // the particle itself
+    if (OP == AB_OP_SPH_DENSITY) a0 = fmaf(pi.w, P.wend_a, a0);   // the particle itself
     o.out[__ldg(P.perm + s)] = a0;
 }
 
