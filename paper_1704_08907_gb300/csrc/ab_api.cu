@@ -489,9 +489,9 @@ ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const fl
     cudaSetDevice(c->device);
     cudaError_t e;
     if ((s = ensure_sv(c, n)) != AB_OK) return s;
-    if ((e = ab::launch_gather_vars(c->cl, op == AB_OP_GAUSS ? w : nullptr, grad_out, c->sc.sv,
-                                    c->stream)) != cudaSuccess)
-        return cuda_fail(c, e, "ab_pair_sum_bwd gather");
+    e = op == AB_OP_GAUSS ? ab::launch_gather_vars(c->cl, w, grad_out, c->sc.sv, c->stream)
+                          : ab::launch_gather_w_pos(c->cl, grad_out, c->stream);   // LJ: g only
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd gather");
     ab::PairOut o;
     o.grad_pos = (float4*)grad_pos4;
     o.grad_w = op == AB_OP_GAUSS ? grad_w : nullptr;

@@ -385,12 +385,14 @@ k_pair_bwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float2 vi = live ? __ldg(P.sv + s) : make_float2(0.f, 0.f);
+    // GAUSS: (w, g) per particle from sv; LJ: only g, which rides in the pad
+    // component of the sorted positions (no second load per pair)
+    const float2 vi = (live && OP == AB_OP_GAUSS) ? __ldg(P.sv + s) : make_float2(0.f, 0.f);
     float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f;
     if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
-        [&](uint32_t j, const float4&, float dx, float dy, float dz, float d2) {
-            const float2 vj = __ldg(P.sv + j);
+        [&](uint32_t j, const float4& pj, float dx, float dy, float dz, float d2) {
             if (OP == AB_OP_GAUSS) {
+                const float2 vj = __ldg(P.sv + j);
                 const float k = ex2_approx(-P.s_log2e * d2);
                 const float coef = fmaf(vi.y, vj.x, vj.y * vi.x) * k;
                 gx = fmaf(coef, dx, gx);
@@ -402,7 +404,7 @@ k_pair_bwd(PairParams P, PairOut o) {
                 const float inv = rcp_approx(d2);
                 const float sr2 = P.sig2 * inv;
                 const float sr6 = sr2 * sr2 * sr2;
-                const float coef = (vi.y + vj.y) * (sr6 * fmaf(6.0f, sr6, -3.0f)) * inv;
+                const float coef = (pi.w + pj.w) * (sr6 * fmaf(6.0f, sr6, -3.0f)) * inv;
                 gx = fmaf(coef, dx, gx);
                 gy = fmaf(coef, dy, gy);
                 gz = fmaf(coef, dz, gz);
