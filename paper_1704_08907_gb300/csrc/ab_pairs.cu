@@ -237,8 +237,10 @@ __device__ __forceinline__ float pred_d2(const Geom& g, const float4& pi, const 
 
 // Direct visit: f(j, pj, dx, dy, dz, d2) for every accepted pair, with value
 // separations accurate to one rounding (see value_sep).  Used by every pair
-// kernel.
-template <int DIM, bool GENERAL, class F>
+// kernel.  UNROLL is the unroll factor of the candidate loop, measured per
+// kernel: 2 where the body is short or rarely taken (forwards, COUNT, the
+// fused LJ kernel), 4 for the adjoints and the EXPF / SOFT forces.
+template <int DIM, bool GENERAL, int UNROLL = 4, class F>
 __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
                                             const float4& pi, F&& f) {
     const Geom& g = P.g;
@@ -262,7 +264,7 @@ __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
                 }
             }
         } else {
-#pragma unroll 4
+#pragma unroll UNROLL
             for (uint32_t j = a; j < b; ++j) {
                 const float4 pj = __ldg(P.spos + j);
                 float dx, dy, dz;
@@ -303,7 +305,7 @@ k_pair_fwd(PairParams P, PairOut o) {
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
     float a0 = 0.0f;
-    visit_pairs<DIM, GENERAL>(P, s, pi,
+    visit_pairs<DIM, GENERAL, 2>(P, s, pi,
         [&](uint32_t, const float4& pj, float, float, float, float d2) {
             if (OP == AB_OP_COUNT) {
                 a0 += 1.0f;
@@ -329,7 +331,7 @@ k_pair_fwd_q(PairParams P, PairOut o) {
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
     const float ai = (OP == AB_OP_SPH_FORCE && live) ? __ldg(&P.sv[s].y) : 0.0f;
-    if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
+    if (live) visit_pairs<DIM, GENERAL, (OP == AB_OP_EXPF || OP == AB_OP_SOFT) ? 4 : 2>(P, s, pi,
         [&](uint32_t j, const float4&, float dx, float dy, float dz, float d2) {
             if (OP == AB_OP_SPH_FORCE) {
                 // m_j (A_i + A_j) W'(d)/d dx, W'(d)/d = wend_grad t^3
@@ -440,7 +442,7 @@ k_pair_lj_eg(PairParams P, PairOut o) {
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     float e = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
-    if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
+    if (live) visit_pairs<DIM, GENERAL, 2>(P, s, pi,
         [&](uint32_t, const float4&, float dx, float dy, float dz, float d2) {
             const float inv = rcp_approx(d2);
             const float sr2 = P.sig2 * inv;
@@ -477,7 +479,7 @@ k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
     uint32_t c = 0;
-    visit_pairs<DIM, GENERAL>(P, s, pi,
+    visit_pairs<DIM, GENERAL, 2>(P, s, pi,
         [&](uint32_t, const float4&, float, float, float, float) { ++c; });
     counts[__ldg(P.perm + s)] = c;
 }
@@ -489,7 +491,7 @@ k_pair_emit(PairParams P, const int64_t* __restrict__ offsets, int32_t* __restri
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
     int64_t at = offsets[__ldg(P.perm + s)];
-    visit_pairs<DIM, GENERAL>(P, s, pi,
+    visit_pairs<DIM, GENERAL, 2>(P, s, pi,
         [&](uint32_t j, const float4&, float, float, float, float) {
             idx[at++] = (int32_t)__ldg(P.perm + j);
         });
