@@ -842,13 +842,15 @@ k_prep_rows64(int64_t rows, int ncols, const float* __restrict__ src, int64_t bl
     }
 }
 
-// Centred points for the gradient, y~ = y - c, in pairs (2p, 2p + 1) as two
-// float4 (x0, x1, y0, y1), (z0, z1, 0, 0), so the epilogue reads a column
-// pair's components as packed FP32 pairs.  Padding points are 0; their
-// column of S = G W^T is exactly 0 (zero rows of W), so they add nothing.
+// Centred, scaled points for the gradient, y~ = q (y - c) with q = sqrt(s'),
+// s' = s log2(e), so that |x~ - y~|^2 is the base-2 exponent's magnitude
+// directly; in pairs (2p, 2p + 1) as two float4 (x0, x1, y0, y1),
+// (z0, z1, 0, 0), so the epilogue reads a column pair's components as
+// packed FP32 pairs.  Padding points are 0; their column of S = G W^T is
+// exactly 0 (zero rows of W), so they add nothing.
 __global__ void __launch_bounds__(256)
 k_prep_ytil(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_t* __restrict__ bbox,
-            float4* __restrict__ Yt, float4* __restrict__ centre) {
+            float q, float4* __restrict__ Yt, float4* __restrict__ centre) {
     const float c0 = 0.5f * (ord2f(bbox[0]) + ord2f(bbox[4]));
     const float c1 = 0.5f * (ord2f(bbox[1]) + ord2f(bbox[5]));
     const float c2 = 0.5f * (ord2f(bbox[2]) + ord2f(bbox[6]));
@@ -862,7 +864,7 @@ k_prep_ytil(int64_t n, const float4* __restrict__ Y, int64_t npad, const uint32_
             h[u] = make_float3(0.0f, 0.0f, 0.0f);
             if (j < n) {
                 const float4 y = __ldg(Y + j);
-                h[u] = make_float3(y.x - c0, y.y - c1, y.z - c2);
+                h[u] = make_float3(q * (y.x - c0), q * (y.y - c1), q * (y.z - c2));
             }
         }
         Yt[2 * p] = make_float4(h[0].x, h[1].x, h[0].y, h[1].y);
@@ -992,13 +994,14 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         // (lane / 4, lane % 4) holds rows 16 h + 8 u + g4 (u = 0, 1) of the
         // quadrant at column pairs 8 k + 2 c4 (the 16x256b TMEM load layout):
         // one y~ load serves two rows, and every step works on column pairs
-        // with packed FP32 arithmetic.  The exponent is formed from the
-        // differences d = x~ - y~ that the sums need anyway:
-        // -s' |d|^2 (base 2), K = 2^that.
+        // with packed FP32 arithmetic.  Coordinates are scaled by sqrt(s'),
+        // so the exponent comes from the differences d = x~ - y~ that the
+        // sums need anyway: K = 2^-|d|^2.
         const int quad = warp & 3, half = (warp >> 2) & 1, cpart = warp >> 3;
         const int g4 = lane >> 2, c4 = lane & 3;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32 + 16 * half) << 16);
         uint64_t xt[2][3];   // row u: x~ components as duplicated pairs (padding rows: S = 0)
+        const float qs = sqrtf(sl2e);   // the scale of the y~ image
         {
             const float4 c = __ldg(centre);
 #pragma unroll
@@ -1007,16 +1010,15 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 float a = 0.f, bb = 0.f, cc = 0.f;
                 if (row < m) {
                     const float4 x = __ldg(X + row);
-                    a = x.x - c.x;
-                    bb = x.y - c.y;
-                    cc = x.z - c.z;
+                    a = qs * (x.x - c.x);
+                    bb = qs * (x.y - c.y);
+                    cc = qs * (x.z - c.z);
                 }
                 xt[u][0] = f2pack(a, a);
                 xt[u][1] = f2pack(bb, bb);
                 xt[u][2] = f2pack(cc, cc);
             }
         }
-        const uint64_t nsl2 = f2pack(-sl2e, -sl2e);
         // per row: sums of A dx, A dy, A dz and A * exponent, even and odd
         // columns in the two halves of each packed pair
         uint64_t acc[2][4];
@@ -1047,15 +1049,14 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                     for (int u = 0; u < 2; ++u) {
                         const uint64_t d0 = sub2(xt[u][0], yx), d1 = sub2(xt[u][1], yy);
                         const uint64_t d2 = sub2(xt[u][2], yz);
-                        uint64_t e = mul2(d0, d0);
+                        uint64_t e = mul2(d0, d0);   // s' |x - y|^2: K = 2^-e
                         e = fma2(d1, d1, e);
                         e = fma2(d2, d2, e);
-                        e = mul2(e, nsl2);
                         float e0, e1;
                         f2unpack(e, e0, e1);
                         const uint64_t A = mul2(f2pack(__uint_as_float(v[4 * k + 2 * u]),
                                                        __uint_as_float(v[4 * k + 2 * u + 1])),
-                                                f2pack(ex2f_tc(e0), ex2f_tc(e1)));
+                                                f2pack(ex2f_tc(-e0), ex2f_tc(-e1)));
                         acc[u][0] = fma2(A, d0, acc[u][0]);
                         acc[u][1] = fma2(A, d1, acc[u][1]);
                         acc[u][2] = fma2(A, d2, acc[u][2]);
@@ -1102,12 +1103,14 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             se += red[(pp * 128 + i) * 4 + 3];
         }
         if (row0 + i < m && dX && !*abort_flag) {
-            const float4 g = make_float4(-2.0f * s * sx, -2.0f * s * sy, -2.0f * s * sz, 0.0f);
+            // the sums carry the scale q of the differences
+            const float f = -2.0f * s / sqrtf(sl2e);
+            const float4 g = make_float4(f * sx, f * sy, f * sz, 0.0f);
             if (gridDim.y == 1) dX[row0 + i] = g;
             else atomicAdd(dX + row0 + i, g);
         }
-        // ds = -sum A d2 = (1/s') sum A * exponent, exponent = -s' d2
-        double v = (row0 + i < m) ? (double)se / (double)sl2e : 0.0;
+        // ds = -sum A d2 = -(1/s') sum A e, e = s' d2
+        double v = (row0 + i < m) ? -(double)se / (double)sl2e : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         __shared__ double wsum[4];
@@ -1219,7 +1222,8 @@ cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* X, const f
     k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const float sl2e = s * kLog2eTC;
-    k_prep_ytil<<<(unsigned)((nb * 64 + 255) / 256), 256, 0, st>>>(n, Y, nb * 128, bbox, Yt, centre);
+    k_prep_ytil<<<(unsigned)((nb * 64 + 255) / 256), 256, 0, st>>>(n, Y, nb * 128, bbox, sqrtf(sl2e), Yt,
+                                                                   centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int split = (mb < 4 * (int64_t)g_num_sms && nb >= 2) ? 2 : 1;
     if (split == 2 && dX && (e = cudaMemsetAsync(dX, 0, (size_t)m * sizeof(float4), st)) != cudaSuccess)
