@@ -489,8 +489,10 @@ ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const fl
     cudaSetDevice(c->device);
     cudaError_t e;
     if ((s = ensure_sv(c, n)) != AB_OK) return s;
-    e = op == AB_OP_GAUSS ? ab::launch_gather_vars(c->cl, w, grad_out, c->sc.sv, c->stream)
-                          : ab::launch_gather_w_pos(c->cl, grad_out, c->stream);   // LJ: g only
+    // g into the pad of the sorted positions; GAUSS also needs w, as float[n]
+    e = ab::launch_gather_w_pos(c->cl, grad_out, c->stream);
+    if (e == cudaSuccess && op == AB_OP_GAUSS)
+        e = ab::launch_gather_scalar(c->cl, w, reinterpret_cast<float*>(c->sc.sv), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd gather");
     ab::PairOut o;
     o.grad_pos = (float4*)grad_pos4;

@@ -386,6 +386,21 @@ cudaError_t launch_gather_vars(const CellList& cl, const float* w, const float* 
     return cudaGetLastError();
 }
 
+// A per-particle scalar in sorted order: out[s] = v[perm[s]].
+__global__ void __launch_bounds__(kThreads)
+k_gather_scalar(int64_t n, const uint32_t* __restrict__ perm, const float* __restrict__ v,
+                float* __restrict__ out) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        out[s] = __ldg(v + perm[s]);
+}
+
+cudaError_t launch_gather_scalar(const CellList& cl, const float* v, float* out, cudaStream_t st) {
+    if (cl.n <= 0) return cudaSuccess;
+    k_gather_scalar<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, v, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st) {
     if (cl.n <= 0) return cudaSuccess;
     k_gather_w_pos<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, w, cl.spos);

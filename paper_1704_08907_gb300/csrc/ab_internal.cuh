@@ -82,6 +82,8 @@ struct Scratch {
 AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
                                    uint32_t* err, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st);
+AB_HIDDEN cudaError_t launch_gather_scalar(const CellList& cl, const float* v, float* out,
+                                           cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_vars(const CellList& cl, const float* w,
                                          const float* g, float2* sv,
                                          cudaStream_t st);

@@ -387,21 +387,22 @@ k_pair_bwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // GAUSS: (w, g) per particle from sv; LJ: only g, which rides in the pad
-    // component of the sorted positions (no second load per pair)
-    const float2 vi = (live && OP == AB_OP_GAUSS) ? __ldg(P.sv + s) : make_float2(0.f, 0.f);
+    // the upstream gradient g rides in the pad component of the sorted
+    // positions; GAUSS also needs w, a float per particle (sv as float[n])
+    const float* __restrict__ wv = reinterpret_cast<const float*>(P.sv);
+    const float wi = (live && OP == AB_OP_GAUSS) ? __ldg(wv + s) : 0.0f;
     float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f;
     if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
         [&](uint32_t j, const float4& pj, float dx, float dy, float dz, float d2) {
             if (OP == AB_OP_GAUSS) {
-                const float2 vj = __ldg(P.sv + j);
+                const float wj = __ldg(wv + j);
                 const float k = ex2_approx(-P.s_log2e * d2);
-                const float coef = fmaf(vi.y, vj.x, vj.y * vi.x) * k;
+                const float coef = fmaf(pi.w, wj, pj.w * wi) * k;
                 gx = fmaf(coef, dx, gx);
                 gy = fmaf(coef, dy, gy);
                 gz = fmaf(coef, dz, gz);
-                dw = fmaf(vj.y, k, dw);
-                ds = fmaf(vj.x * k, d2, ds);
+                dw = fmaf(pj.w, k, dw);
+                ds = fmaf(wj * k, d2, ds);
             } else {  // LJ: 1/2 (g_i + g_j) eps (12 sr12 - 6 sr6) / d2
                 const float inv = rcp_approx(d2);
                 const float sr2 = P.sig2 * inv;
@@ -425,7 +426,7 @@ k_pair_bwd(PairParams P, PairOut o) {
         }
     }
     if (OP == AB_OP_GAUSS && o.partial)
-        block_partial<kPairThreads>(live ? -(double)vi.y * (double)ds : 0.0, o.partial);
+        block_partial<kPairThreads>(live ? -(double)pi.w * (double)ds : 0.0, o.partial);
 }
 
 // LJ energy and its gradient in one walk, for a loss equal to the total
