@@ -99,17 +99,6 @@ k_finalize(int64_t n, const float* __restrict__ pos,
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_gather_vars(int64_t n, const uint32_t* __restrict__ perm,
-              const float* __restrict__ w, const float* __restrict__ g,
-              float2* __restrict__ sv) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t p = perm[s];
-        sv[s] = make_float2(w ? __ldg(w + p) : 0.0f, g ? __ldg(g + p) : 0.0f);
-    }
-}
-
 // The per-particle weight w, in sorted order, into the pad component of the
 // sorted positions: a forward that needs only w (Gaussian sum, SPH density)
 // then reads it with the candidate's position, no separate load.
@@ -377,13 +366,6 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-cudaError_t launch_gather_vars(const CellList& cl, const float* w, const float* g,
-                               float2* sv, cudaStream_t st) {
-    if (cl.n <= 0) return cudaSuccess;
-    k_gather_vars<<<ew_grid(cl.n), kThreads, 0, st>>>(cl.n, cl.perm, w, g, sv);
-    return cudaGetLastError();
 }
 
 // A per-particle scalar in sorted order: out[s] = v[perm[s]].

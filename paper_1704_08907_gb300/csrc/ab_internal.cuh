@@ -84,9 +84,6 @@ AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, 
 AB_HIDDEN cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_scalar(const CellList& cl, const float* v, float* out,
                                            cudaStream_t st);
-AB_HIDDEN cudaError_t launch_gather_vars(const CellList& cl, const float* w,
-                                         const float* g, float2* sv,
-                                         cudaStream_t st);
 // sv[s] = wv[perm[s]]: a per-particle pair of values into sorted order
 AB_HIDDEN cudaError_t launch_gather_pairs(const CellList& cl, const float2* wv, float2* sv,
                                           cudaStream_t st);
