@@ -239,7 +239,7 @@ ab_status ab_destroy(ab_ctx* c) {
     if (!c) return AB_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_id, c->cl.rank, c->cl.tmp,
+    void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_rank, c->cl.tmp,
                     c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
                     c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws};
     for (void* b : bufs)
@@ -294,9 +294,10 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
     if (nn > cl.cap_n || !cl.spos) {
         // all per-particle buffers share one capacity
         const size_t want = nn + nn / 4 + 64;
-        void* fresh[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t bytes[5] = {16, 4, 4, 4, 8};   // tmp: (original index, cell) pairs
-        for (int t = 0; t < 5; ++t) {
+        void* fresh[4] = {nullptr, nullptr, nullptr, nullptr};
+        // spos, perm, (cell, rank) per particle, tmp: (original index, cell) per slot
+        const size_t bytes[4] = {16, 4, 8, 8};
+        for (int t = 0; t < 4; ++t) {
             e = cudaMallocAsync(&fresh[t], want * bytes[t], c->stream);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -304,14 +305,13 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
                 return cuda_fail(c, e, "ab_build (particle buffers)");
             }
         }
-        void* old[5] = {cl.spos, cl.perm, cl.cell_id, cl.rank, cl.tmp};
+        void* old[4] = {cl.spos, cl.perm, cl.cell_rank, cl.tmp};
         for (void* b : old)
             if (b) cudaFreeAsync(b, c->stream);
         cl.spos = (float4*)fresh[0];
         cl.perm = (uint32_t*)fresh[1];
-        cl.cell_id = (uint32_t*)fresh[2];
-        cl.rank = (uint32_t*)fresh[3];
-        cl.tmp = (uint32_t*)fresh[4];
+        cl.cell_rank = (uint2*)fresh[2];
+        cl.tmp = (uint32_t*)fresh[3];
         cl.cap_n = want;
     }
     if ((e = grow(&cl.cell_start, &cl.cap_cells, (size_t)g.n_cells + 1, c->stream)) != cudaSuccess)

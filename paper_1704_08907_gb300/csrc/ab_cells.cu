@@ -44,8 +44,7 @@ __device__ __forceinline__ float4 load_pos(const float* __restrict__ pos, int64_
 // ---------------------------------------------------------------------------
 template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kThreads)
-k_hash(const float* __restrict__ pos, int64_t n, Geom g,
-       uint32_t* __restrict__ cell_id, uint32_t* __restrict__ rank,
+k_hash(const float* __restrict__ pos, int64_t n, Geom g, uint2* __restrict__ cell_rank,
        uint32_t* __restrict__ count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -57,20 +56,18 @@ k_hash(const float* __restrict__ pos, int64_t n, Geom g,
             uint32_t cz = (uint32_t)cell_coord(p.z, g.lo[2], g.inv_w[2], g.n[2]);
             c += (uint32_t)g.n[0] * (uint32_t)g.n[1] * cz;
         }
-        cell_id[i] = c;
-        rank[i] = atomicAdd(count + c, 1u);
+        cell_rank[i] = make_uint2(c, atomicAdd(count + c, 1u));
     }
 }
 
 // (a3) scatter (original index, cell) into the particle's (unordered) slot.
 __global__ void __launch_bounds__(kThreads)
-k_scatter(int64_t n, const uint32_t* __restrict__ cell_id,
-          const uint32_t* __restrict__ rank,
+k_scatter(int64_t n, const uint2* __restrict__ cell_rank,
           const uint32_t* __restrict__ cell_start, uint2* __restrict__ tmp) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c = cell_id[i];
-        tmp[cell_start[c] + rank[i]] = make_uint2((uint32_t)i, c);
+        const uint2 cr = cell_rank[i];
+        tmp[cell_start[cr.x] + cr.y] = make_uint2((uint32_t)i, cr.x);
     }
 }
 
@@ -339,11 +336,11 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
     if (n > 0) {
         const int gr = ew_grid(n);
         if (cl.g.dim == 3) {
-            if (packed) k_hash<3, true><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
-            else k_hash<3, false><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+            if (packed) k_hash<3, true><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_rank, cl.cell_start);
+            else k_hash<3, false><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_rank, cl.cell_start);
         } else {
-            if (packed) k_hash<2, true><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
-            else k_hash<2, false><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_id, cl.rank, cl.cell_start);
+            if (packed) k_hash<2, true><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_rank, cl.cell_start);
+            else k_hash<2, false><<<gr, kThreads, 0, st>>>(pos, n, cl.g, cl.cell_rank, cl.cell_start);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -353,7 +350,7 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
     if (e != cudaSuccess) return e;
     if (n > 0) {
         uint2* tmp = reinterpret_cast<uint2*>(cl.tmp);   // 8 bytes a particle
-        k_scatter<<<ew_grid(n), kThreads, 0, st>>>(n, cl.cell_id, cl.rank, cl.cell_start, tmp);
+        k_scatter<<<ew_grid(n), kThreads, 0, st>>>(n, cl.cell_rank, cl.cell_start, tmp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int gr = ew_grid(n);
         if (cl.g.dim == 3) {

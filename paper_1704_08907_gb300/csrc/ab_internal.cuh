@@ -53,8 +53,7 @@ struct CellList {
     bool valid = false;
     float4* spos = nullptr;           // sorted positions (x, y, z, 0)
     uint32_t* perm = nullptr;         // perm[s] = original index
-    uint32_t* cell_id = nullptr;      // per original particle
-    uint32_t* rank = nullptr;         // per original particle (atomic rank)
+    uint2* cell_rank = nullptr;       // per original particle: (cell, atomic arrival rank)
     uint32_t* tmp = nullptr;          // unordered slot -> original index
     uint32_t* cell_start = nullptr;   // [n_cells + 1]
     size_t cap_n = 0, cap_cells = 0;
