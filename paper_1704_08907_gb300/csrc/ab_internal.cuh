@@ -60,7 +60,8 @@ struct CellList {
 };
 
 struct Scratch {
-    float2* sv = nullptr;             // sorted per-particle (w, g)
+    float2* sv = nullptr;             // sorted per-particle values: (m, P/rho^2) for the SPH
+                                      // force, or w as float[n] for the Gaussian adjoint
     size_t cap_sv = 0;
     uint64_t* scan_status = nullptr;  // decoupled look-back tile words
     uint32_t* scan_ticket = nullptr;
