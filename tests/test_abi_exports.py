@@ -58,3 +58,28 @@ def test_status_strings_without_gpu():
     for s in range(9):
         assert lib.ab_status_string(s)
     assert lib.ab_status_string(99) == b"unknown status"
+
+
+def _declared_arity():
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ab_\w+)\s*\(([^;{]*?)\)\s*;", txt, re.M | re.S):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_headers():
+    """Every ctypes signature has exactly the parameters its declaration has
+    (a missing or extra argument would pass garbage across the boundary)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_abi", os.path.join(ROOT, "paper_1704_08907_gb300", "_abi.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    arity = _declared_arity()
+    assert set(arity) == _declared()
+    bad = {n: (arity[n], len(mod.SIGNATURES[n][1])) for n in arity
+           if arity[n] != len(mod.SIGNATURES[n][1])}
+    assert not bad, bad
