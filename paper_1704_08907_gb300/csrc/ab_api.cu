@@ -15,7 +15,21 @@
 #include "../../include/aboria_gpu_testing.h"
 
 namespace ab {
-int g_num_sms = 152;
+// SM count of the current device, looked up once per device (the cache write
+// is idempotent, so concurrent first calls are harmless).
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] <= 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            return 152;
+        cache[dev] = sms;
+    }
+    return cache[dev];
+}
 }
 
 struct ab_ctx {
@@ -219,9 +233,6 @@ ab_status ab_create(ab_ctx** out, int device, void* stream) {
     }
     if (device < 0 || device >= count) return AB_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return AB_ERR_CUDA;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
-        ab::g_num_sms = sms;
     ab_ctx* c = new ab_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;

@@ -25,7 +25,6 @@
 
 namespace ab {
 
-extern int g_num_sms;
 
 namespace {
 
@@ -168,7 +167,7 @@ cudaError_t launch_md_step(const Geom& geo, int64_t n, float4* pos, float4* vel,
                            const float4* acc, float dt, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
-    const int64_t cap = (int64_t)g_num_sms * 8;
+    const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
     k_md_step<<<(unsigned)blocks, 256, 0, st>>>(n, pos, vel, acc, step_geom(geo), dt);
     return cudaGetLastError();
@@ -181,7 +180,7 @@ cudaError_t launch_bd_step(const Geom& geo, int64_t n, float4* pos, const float4
     const StepGeom g = step_geom(geo);
     const float amp = (float)sqrt(2.0 * (double)D * (double)dt);
     int64_t blocks = (n + 255) / 256;
-    const int64_t cap = (int64_t)g_num_sms * 8;
+    const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
     k_bd_step<<<(unsigned)blocks, 256, 0, st>>>(n, pos, force, g, dt, amp, seed, step);
     return cudaGetLastError();

@@ -13,7 +13,6 @@
 
 namespace ab {
 
-extern int g_num_sms;
 
 namespace {
 
@@ -24,7 +23,7 @@ inline int ew_grid(int64_t n) {
     // latency-bound (dependent loads and atomics), so they want many loads in
     // flight rather than long grid-stride loops
     int64_t b = (n + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)g_num_sms * 64;
+    int64_t cap = (int64_t)num_sms() * 64;
     if (b > cap) b = cap;
     return b < 1 ? 1 : (int)b;
 }

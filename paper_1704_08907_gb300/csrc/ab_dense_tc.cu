@@ -36,7 +36,6 @@
 
 namespace ab {
 
-extern int g_num_sms;
 
 namespace {
 
@@ -1171,7 +1170,7 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     const int64_t mblocks = (m + kTM - 1) / kTM;
     // split the Y range in two when the row blocks alone leave a ragged last
     // wave (fewer than four waves of one CTA per SM)
-    const int split = (mblocks < 4 * (int64_t)g_num_sms && tiles >= 2) ? 2 : 1;
+    const int split = (mblocks < 4 * (int64_t)num_sms() && tiles >= 2) ? 2 : 1;
     if (split == 2 && (e = cudaMemsetAsync(out, 0, (size_t)m * nrhs * sizeof(float), st)) != cudaSuccess)
         return e;
     // set on every launch: the attribute belongs to the current device, and
@@ -1225,7 +1224,7 @@ cudaError_t launch_dense_tc_gradx(int64_t m, int64_t n, const float4* X, const f
     k_prep_ytil<<<(unsigned)((nb * 64 + 255) / 256), 256, 0, st>>>(n, Y, nb * 128, bbox, sqrtf(sl2e), Yt,
                                                                    centre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int split = (mb < 4 * (int64_t)g_num_sms && nb >= 2) ? 2 : 1;
+    const int split = (mb < 4 * (int64_t)num_sms() && nb >= 2) ? 2 : 1;
     if (split == 2 && dX && (e = cudaMemsetAsync(dX, 0, (size_t)m * sizeof(float4), st)) != cudaSuccess)
         return e;
     const dim3 grid((unsigned)mb, (unsigned)split);

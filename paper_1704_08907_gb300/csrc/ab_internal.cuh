@@ -113,6 +113,7 @@ struct PairOut {
     int partial_count = 0;
 };
 AB_HIDDEN int pair_grid(int64_t n);
+AB_HIDDEN int num_sms();   // SM count of the current device
 AB_HIDDEN cudaError_t launch_pair_fwd(const CellList& cl, ab_op op,
                                       const ab_op_params& prm, const float2* sv,
                                       PairOut& o, cudaStream_t st);
