@@ -34,8 +34,12 @@
  *    positions into the library's sorted workspace, so later pair sums do
  *    not read the caller's position array and may overwrite it.
  *  - The context owns its workspace (cell table, sorted copies, scan state)
- *    and grows it on demand with cudaMalloc; AB_ERR_OOM leaves the context
+ *    and grows it on demand with cudaMallocAsync on the context's stream
+ *    (the device's default memory pool); AB_ERR_OOM leaves the context
  *    usable with its previous workspace.
+ *  - Each call makes the context's device current while it runs and
+ *    restores the caller's current device before it returns; a failure to
+ *    select the device returns AB_ERR_CUDA.
  *  - A context is not thread-safe; use one per host thread / stream.
  */
 #ifndef ABORIA_GPU_H

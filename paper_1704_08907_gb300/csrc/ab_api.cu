@@ -9,27 +9,52 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 
 #include "ab_internal.cuh"
 #include "../../include/aboria_gpu_testing.h"
 
 namespace ab {
-// SM count of the current device, looked up once per device (the cache write
-// is idempotent, so concurrent first calls are harmless).
+// SM count of the current device, looked up once per device.  The cache
+// entries are atomics: concurrent first calls store the same value.
 int num_sms() {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (cache[dev] <= 0) {
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms <= 0)
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            v <= 0)
             return 152;
-        cache[dev] = sms;
+        cache[dev].store(v, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return v;
 }
+
+// Makes the context's device current for one entry point and restores the
+// caller's current device on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false, switched = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev == dev) {
+            ok = true;
+            return;
+        }
+        ok = switched = cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (switched && prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
 }
 
 struct ab_ctx {
@@ -232,7 +257,8 @@ ab_status ab_create(ab_ctx** out, int device, void* stream) {
         return AB_ERR_CUDA;
     }
     if (device < 0 || device >= count) return AB_ERR_INVALID_ARG;
-    if (cudaSetDevice(device) != cudaSuccess) return AB_ERR_CUDA;
+    ab::DeviceGuard dg(device);
+    if (!dg.ok) return AB_ERR_CUDA;
     ab_ctx* c = new ab_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
@@ -248,7 +274,7 @@ ab_status ab_create(ab_ctx** out, int device, void* stream) {
 
 ab_status ab_destroy(ab_ctx* c) {
     if (!c) return AB_OK;
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_rank, c->cl.tmp,
                     c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
@@ -270,7 +296,8 @@ ab_status ab_set_stream(ab_ctx* c, void* stream) {
 
 ab_status ab_sync(ab_ctx* c) {
     if (!c) return AB_ERR_INVALID_ARG;
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_sync");
     uint32_t h = 0;
@@ -296,7 +323,8 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
         return fail(c, AB_ERR_INVALID_ARG, "pos4 must be a 16-byte aligned device pointer");
     if (packed && n > 0 && (!pos || ((uintptr_t)pos & 3)))
         return fail(c, AB_ERR_INVALID_ARG, "pos must be a 4-byte aligned device pointer");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     CellList& cl = c->cl;
     cl.valid = false;
     Geom g = make_geom(dom, n);
@@ -365,7 +393,8 @@ ab_status ab_cell_export(ab_ctx* c, uint32_t* perm, uint32_t* cell_start) {
     if (!c) return AB_ERR_INVALID_ARG;
     ab_status s = require_cells(c);
     if (s != AB_OK) return s;
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e = cudaSuccess;
     if (perm && c->cl.n > 0)
         e = cudaMemcpyAsync(perm, c->cl.perm, (size_t)c->cl.n * 4, cudaMemcpyDeviceToDevice, c->stream);
@@ -397,7 +426,8 @@ ab_status ab_pair_sum(ab_ctx* c, ab_op op, const ab_op_params* prm, const float*
     if ((uses_w && overlaps(out, ob, w, wb)) || (uses_w && overlaps(energy, 8, w, wb)) ||
         overlaps(energy, 8, out, ob))
         return fail(c, AB_ERR_ALIAS, "output overlaps an input");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e;
     if (op == AB_OP_SPH_FORCE) {
         if ((s = ensure_sv(c, n)) != AB_OK) return s;
@@ -442,7 +472,8 @@ static ab_status energy_grad_impl(ab_ctx* c, ab_op op, const ab_op_params* prm, 
     if (overlaps(E, (size_t)n * 4, grad, gbytes) ||
         overlaps(energy, 8, E, (size_t)n * 4) || overlaps(energy, 8, grad, gbytes))
         return fail(c, AB_ERR_ALIAS, "outputs overlap");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     ab::PairOut o;
     o.out = E;
     if (packed) o.grad_packed = grad;
@@ -497,7 +528,8 @@ ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const fl
     if (overlaps(grad_pos4, n16, grad_w, n4) || overlaps(grad_s, 8, grad_pos4, n16) ||
         overlaps(grad_s, 8, grad_w, n4))
         return fail(c, AB_ERR_ALIAS, "outputs overlap");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e;
     if ((s = ensure_sv(c, n)) != AB_OK) return s;
     // g into the pad of the sorted positions; GAUSS also needs w, as float[n]
@@ -534,7 +566,8 @@ ab_status ab_pair_list(ab_ctx* c, int64_t* offsets, int32_t* idx, int64_t cap, i
         return fail(c, AB_ERR_INVALID_ARG, "offsets, nnz required; idx required when cap > 0");
     if (overlaps(offsets, (size_t)(n + 1) * 8, idx, (size_t)cap * 4))
         return fail(c, AB_ERR_ALIAS, "offsets overlap idx");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e = grow(&c->sc.counts, &c->sc.cap_counts, (size_t)n + 1, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_list workspace");
     if ((s = ensure_scan(c, n + 1)) != AB_OK) return s;
@@ -576,7 +609,8 @@ ab_status ab_kernel_matvec(ab_ctx* c, int64_t m, int64_t n, const float* X, cons
     if (overlaps(out, ob, X, (size_t)m * 16) || overlaps(out, ob, Y, (size_t)n * 16) ||
         overlaps(out, ob, W, (size_t)n * nrhs * 4))
         return fail(c, AB_ERR_ALIAS, "out overlaps an input");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e;
     if (prec == AB_PREC_FP32) {
         e = ab::launch_dense_fwd(m, n, (const float4*)X, (const float4*)Y, nrhs, W, s, prec, out,
@@ -612,7 +646,8 @@ ab_status ab_kernel_solve(ab_ctx* c, int64_t n, const float* X, int32_t nrhs, co
     if (iters) *iters = 0;
     if (relres) *relres = 0.0f;
     if (n == 0) return AB_OK;
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e = grow(&c->sc.solve_ws, &c->sc.cap_solve_ws, ab::solve_workspace_bytes(n, nrhs),
                          c->stream);
     if (e == cudaSuccess && prec != AB_PREC_FP32)
@@ -656,7 +691,8 @@ ab_status ab_kernel_matvec_bwd(ab_ctx* c, int64_t m, int64_t n, const float* X, 
             if (overlaps(outs[a], outb[a], outs[b], outb[b]))
                 return fail(c, AB_ERR_ALIAS, "outputs overlap");
     }
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     double* partial = nullptr;
     if (ds) {
         // SIMT: one partial per 128-row block; tensor cores: up to two per block
@@ -715,7 +751,8 @@ ab_status ab_bd_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4,
         return fail(c, AB_ERR_INVALID_ARG, "dt, D must be finite, D >= 0");
     if (overlaps(pos4, (size_t)n * 16, force4, (size_t)n * 16))
         return fail(c, AB_ERR_ALIAS, "force4 overlaps pos4");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     Geom g = make_geom(dom, 0);
     cudaError_t e = ab::launch_bd_step(g, n, (float4*)pos4, (const float4*)force4, dt, D, seed,
                                        step, c->stream);
@@ -736,7 +773,8 @@ ab_status ab_md_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4, fl
     const size_t b = (size_t)n * 16;
     if (overlaps(pos4, b, vel4, b) || overlaps(pos4, b, acc4, b) || overlaps(vel4, b, acc4, b))
         return fail(c, AB_ERR_ALIAS, "pos4, vel4 and acc4 must not overlap");
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     Geom g = make_geom(dom, 0);
     cudaError_t e = ab::launch_md_step(g, n, (float4*)pos4, (float4*)vel4, (const float4*)acc4, dt,
                                        c->stream);
@@ -752,7 +790,8 @@ ab_status ab_testing_scan_timeout(ab_ctx* c, int64_t items, int32_t skip_tile,
     if (!c || items < 1 || items >= (int64_t(1) << 30) || skip_tile < 0 || limit_ns <= 0 ||
         limit_ns > 2000000000ll)
         return AB_ERR_INVALID_ARG;
-    cudaSetDevice(c->device);
+    ab::DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e = grow(&c->sc.counts, &c->sc.cap_counts, (size_t)items, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "testing scan workspace");
     ab_status s = ensure_scan(c, items);
