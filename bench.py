@@ -33,9 +33,13 @@ import synth  # noqa: E402
 
 METRIC = "pair interactions/s fwd+bwd (3-D LJ, N=2^20, r=0.0197)"
 UNIT = "pairs/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+# Gaussian pair sum (clustered workload): per accepted pair, forward 4 FP32
+# operations + 1 exponential, adjoint twice that (the cost model of the
+# measurement plan: backward ~2x forward)
+OPS_PER_PAIR_GAUSS_FWD = 5
+OPS_PER_PAIR_GAUSS_BWD = 10
 # Algorithmic FP32 operations: per candidate pair the predicate (3 sub, 3 mul,
 # 2 add, 1 compare); per accepted pair the LJ adjoint term (1 reciprocal,
 # 3 mul for (sig/d)^6, 3 for the coefficient, 2 for (g_i + g_j), 3 FMA).
@@ -52,6 +56,40 @@ OPS_PER_PAIR_LJ_EG = 12
 # only for the kernel source it was taken on (None until captured).
 TRAFFIC_EG_BYTES = 35.44e6   # 29.21 MB read + 6.23 MB written
 TRAFFIC_SOURCE_SHA = "3bd5c6d60cbc41b7"
+
+
+def alu_peak(pk):
+    """FP32 lane-operations per second: SMs x 128 lanes x max SM clock, with
+    the SM count read from the device."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    tops = sms * FP32_LANES_PER_SM * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
+    return tops, f"{sms} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x max SM clock"
+
+
+def base_candidates(start_h, ncell, periodic, dim, reach):
+    """Candidates of the paper's method (width-r cells, 3^d stencil): the
+    cell histogram with the kx x-parts of every cell merged back."""
+    kx, ky, kz = reach[0], reach[1], max(reach[2], 1)
+    if dim == 3:
+        cnt = np.diff(start_h.astype(np.int64)).reshape(
+            ncell[2] // kz, kz, ncell[1] // ky, ky, ncell[0] // kx, kx).sum(axis=(1, 3, 5))
+        base = (ncell[0] // kx, ncell[1] // ky, ncell[2] // kz)
+    else:
+        cnt = np.diff(start_h.astype(np.int64)).reshape(
+            ncell[1] // ky, ky, ncell[0] // kx, kx).sum(axis=(1, 3))
+        base = (ncell[0] // kx, ncell[1] // ky, 1)
+    base_start = np.concatenate([[0], np.cumsum(cnt.ravel())])
+    return candidates_from_cells(base_start, base, periodic, dim)
+
+
+def build_bytes(n, n_cells):
+    """Algorithmic DRAM bytes of one cell-list build (the counting sort of the
+    measurement plan): hash = position in (16) + cell id out (4); scatter =
+    cell id in (4) + position in (16) + sorted position out (16) + perm out
+    (4); cell table = count and offset (4 + 4) per cell of width r (the
+    method's cells; finer cells the kernels choose are not counted)."""
+    return n * (16 + 4) + n * (4 + 16 + 16 + 4) + 8 * (n_cells + 1)
 
 
 def peaks():
@@ -204,11 +242,7 @@ def run_ours(args, rank, world):
     # ... and the algorithmic count of the paper's method: width-r cells and
     # the 3^3 stencil (merge the kx x-parts of every cell back together)
     kx, ky, kz = reach
-    cnt = np.diff(start_h.astype(np.int64)).reshape(ncell[2] // kz, kz, ncell[1] // ky, ky,
-                                                      ncell[0] // kx, kx).sum(axis=(1, 3, 5))
-    base_start = np.concatenate([[0], np.cumsum(cnt.ravel())])
-    cands = candidates_from_cells(base_start, (ncell[0] // kx, ncell[1] // ky, ncell[2] // kz),
-                                  w.periodic, 3)
+    cands = base_candidates(start_h, ncell, w.periodic, 3, reach)
 
     # one step: rebuild + LJ energy and its gradient (the forces) in one walk
     def step(ev=None):
@@ -312,14 +346,13 @@ def run_ours(args, rank, world):
     src = os.path.join(ROOT, "paper_1704_08907_gb300", "csrc", "ab_pairs.cu")
     same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC_SOURCE_SHA
     pk, pk_kind = peaks()
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
+    alu, alu_src = alu_peak(pk)
     eg_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_EG
     eg_s = float(np.mean(t_eg)) * 1e-3
     achieved = eg_ops / eg_s / 1e12
     fwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_FWD
     bwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_LJ_BWD
-    build_bytes = n * (16 + 4 + 4) + n * (4 + 4 + 4 + 4) + n * (4 + 4 + 4 + 16 + 4 + 16) \
-        + 8 * (int(np.prod(ncell)) + 1)
+    bbytes = build_bytes(n, int(np.prod(ncell)) // (kx * ky * kz))   # width-r cells
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -332,24 +365,32 @@ def run_ours(args, rank, world):
                    "cell_split": [kx, ky, kz], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "k_pair_lj_eg<3,false>",
-                     "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                     "frac": achieved / alu_peak,
+                     "achieved": achieved, "peak": alu, "unit": "Top/s",
+                     "frac": achieved / alu,
                      "traffic": TRAFFIC_EG_BYTES if same_kernel else None,
                      "algorithmic_ops_per_launch": eg_ops,
-                     "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"},
+                     "peak_source": alu_src},
         "phases_ms": {"build": float(np.mean(t_build)), "energy_and_forces": float(np.mean(t_eg))},
         "phase_roofline": {
-            "build_hbm_gbs": build_bytes / (float(np.mean(t_build)) * 1e-3) / 1e9,
-            "build_hbm_frac": build_bytes / (float(np.mean(t_build)) * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "build_hbm_gbs": bbytes / (float(np.mean(t_build)) * 1e-3) / 1e9,
+            "build_hbm_frac": bbytes / (float(np.mean(t_build)) * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "build_bytes_algorithmic": bbytes,
             "peak_kind": pk_kind},
-        "unfused": {
-            "note": "the same outputs from the separate forward (energy) and adjoint "
-                    "(forces, upstream gradient 1) kernels",
-            "steps": ku, "ms_per_step": u_step, "value": pairs / (u_step * 1e-3),
+        "general_adjoint_step": {
+            "note": "the same workload through the separate forward (per-particle energies) "
+                    "and the general adjoint kernel (any upstream gradient; here 1): the path "
+                    "autograd takes (LJEnergy)",
+            "metric": METRIC, "unit": UNIT, "steps": ku, "ms_per_step": u_step,
+            "value": pairs / (u_step * 1e-3),
             "phases_ms": {"build": float(np.mean(u_build)), "fwd": float(np.mean(u_fwd)),
                           "bwd": float(np.mean(u_bwd))},
-            "fwd_alu_frac": fwd_ops / (float(np.mean(u_fwd)) * 1e-3) / 1e12 / alu_peak,
-            "bwd_alu_frac": bwd_ops / (float(np.mean(u_bwd)) * 1e-3) / 1e12 / alu_peak},
+            "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,LJ> (adjoint)",
+                         "achieved": bwd_ops / (float(np.mean(u_bwd)) * 1e-3) / 1e12,
+                         "peak": alu, "unit": "Top/s",
+                         "frac": bwd_ops / (float(np.mean(u_bwd)) * 1e-3) / 1e12 / alu,
+                         "traffic": None, "peak_source": alu_src},
+            "fwd_alu_frac": fwd_ops / (float(np.mean(u_fwd)) * 1e-3) / 1e12 / alu,
+            "bwd_alu_frac": bwd_ops / (float(np.mean(u_bwd)) * 1e-3) / 1e12 / alu},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": pos_h.numel() * 4,
                 "d2h_bytes_per_step": F_h.numel() * 4 + 8},
@@ -400,11 +441,18 @@ def also_dense(reps=5):
         res[prec] = {"ms": ms, "tflops": 2.0 * m * n * nrhs / (ms * 1e-3) / 1e12}
         outs[prec] = out
     ab.ab_sync(ctx)
-    ref = outs["fp32"].double()
-    scale = ref.abs().max().item()
-    for prec in ("bf16x3", "bf16", "tf32x3", "tf32"):
-        res[prec]["max_abs_diff_vs_fp32_path_over_max"] = \
-            float((outs[prec].double() - ref).abs().max().item() / scale)
+    # error against FP64 for every result: the oracle's FP64 operator on 256
+    # sampled rows, per element over the sum of the magnitudes of the
+    # element's terms (sum_j K_ij |W_jc|)
+    from oracle import dense as odense
+    rows = synth.query_sample(m, 256, 12)
+    ref = odense.matvec(d.X, d.Y, d.W, d.s, rows=rows)
+    den = odense.matvec_abs(d.X, d.Y, d.W, d.s, rows=rows)
+    for prec in ("fp32", "bf16x3", "bf16", "tf32x3", "tf32"):
+        got = outs[prec].cpu().numpy()[rows].astype(np.float64)
+        res[prec]["err_vs_fp64"] = float(np.max(np.abs(got - ref) / den))
+    res["err_vs_fp64_metric"] = ("max over 256 sampled rows x 64 columns of |Y - Y_fp64| / "
+                                 "sum_j K_ij |W_jc| (oracle FP64)")
     res["speedup_bf16x3_vs_fp32"] = res["fp32"]["ms"] / res["bf16x3"]["ms"]
     res["speedup_tf32x3_vs_fp32"] = res["fp32"]["ms"] / res["tf32x3"]["ms"]
     # the BF16X3 forward against the measured bf16 tensor peak: algorithmic
@@ -423,11 +471,33 @@ def also_dense(reps=5):
     dY = torch.empty_like(Y)
     ds = torch.empty((), dtype=torch.float64, device=dev)
     bwd = {}
-    for prec, reps_b in (("fp32", 1), ("bf16x3", reps), ("tf32x3", reps)):
+    cols = synth.query_sample(n, 64, 11)
+    brow = synth.query_sample(m, 64, 10)
+    rW = odense.grad_W(d.X, d.Y, d.G, d.s, cols=cols)
+    aW = odense.grad_W(d.X, d.Y, np.abs(d.G), d.s, cols=cols)
+    rX = odense.grad_X(d.X, d.Y, d.W, d.G, d.s, rows=brow)
+    aX = odense.grad_X_abs(d.X, d.Y, d.W, d.G, d.s, rows=brow)
+    rY = odense.grad_Y(d.X, d.Y, d.W, d.G, d.s, cols=cols)
+    aY = odense.grad_Y_abs(d.X, d.Y, d.W, d.G, d.s, cols=cols)
+
+    def elem(got, r, a):
+        dd = np.maximum(np.abs(r), a)
+        return float(np.max(np.abs(got.astype(np.float64) - r) / dd))
+
+    for prec, reps_b in (("fp32", 1), ("bf16x3", reps), ("bf16", reps), ("tf32x3", reps),
+                         ("tf32", reps)):
         fn = lambda: ab.ab_kernel_matvec_bwd(ctx, X, Y, W, d.s, prec, G, dW, dX, dY, ds)  # noqa: E731
         fn()
         bwd[prec] = {"ms": _timed(fn, reps_b, flush)}
-    ab.ab_sync(ctx)
+        ab.ab_sync(ctx)
+        bwd[prec]["err_vs_fp64"] = {
+            "dW": elem(dW.cpu().numpy()[cols], rW, aW),
+            "dX": elem(dX.cpu().numpy()[brow, :3], rX, aX),
+            "dY": elem(dY.cpu().numpy()[cols, :3], rY, aY)}
+    bwd["err_vs_fp64_metric"] = (
+        "per element over the sum of the magnitudes of its terms (oracle FP64): dW on 64 sampled "
+        "Y rows, dX on 64 sampled X rows, dY on 64 sampled Y rows; ds is checked against the "
+        "FP64 sum at 8192 x 8192 in the tests")
     bwd["speedup_bf16x3_vs_fp32"] = bwd["fp32"]["ms"] / bwd["bf16x3"]["ms"]
     res["adjoint_dW_dX_dY_ds"] = bwd
     res["exps"] = m * n
@@ -436,9 +506,35 @@ def also_dense(reps=5):
     return res
 
 
-def also_c3(reps=5):
+def oracle_sample_c3(w, nq, seed=23):
+    """Oracle Gaussian forward + adjoint (x, w, s) over nq query particles of
+    the clustered workload (cell list over all points).  Returns (pairs in
+    the sample, seconds for the cell list, seconds for the queries, threads)."""
+    import oracle
+    box = oracle.Box(3, w.periodic, w.lo, w.hi, w.radius)
+    q = synth.query_sample(w.n, nq, seed)
+    t0 = time.perf_counter()
+    cl = oracle.CellList(box, w.pos)
+    t1 = time.perf_counter()
+    off, idx = cl.neighbours(q)
+    oracle.pair_values("gauss", box, w.pos, off, idx, q, w=w.w, params=w.params)
+    oracle.pair_grads("gauss", box, w.pos, off, idx, w.g, q, w=w.w, params=w.params)
+    t2 = time.perf_counter()
+    cl.close()
+    return int(off[-1]), t1 - t0, t2 - t1, oracle.num_threads()
+
+
+# DRAM traffic of one k_pair_bwd<3,false,GAUSS> launch on the clustered
+# workload (ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the
+# kernel source whose hash is given (None until captured on that source).
+TRAFFIC_C3_BWD_BYTES = None
+TRAFFIC_C3_SOURCE_SHA = None
+
+
+def also_c3(reps=5, oracle_fraction=64):
     """Clustered 16.7M-point workload: rebuild + Gaussian pair sum + adjoint
-    (x, w, s); pairs per second."""
+    (x, w, s); pairs per second, the adjoint kernel against the ALU roofline,
+    and the oracle on a 1/oracle_fraction query sample on the host cores."""
     import torch
     import paper_1704_08907_gb300 as ab
     w = synth.c3()
@@ -455,6 +551,11 @@ def also_c3(reps=5):
     gs = torch.empty((), dtype=torch.float64, device=dev)
     ab.ab_build(ctx, dom, pos)
     pairs = int(ab.ab_pair_sum(ctx, "count", ab.OpParams()).double().sum().item())
+    ncell, ncells, reach = ab.ab_cell_shape(ctx, with_reach=True)
+    _, start = ab.ab_cell_export(ctx)
+    start_h = start.cpu().numpy().view(np.uint32)
+    cands = base_candidates(start_h, ncell, w.periodic, 3, reach)
+    del start, start_h
 
     def step():
         ab.ab_build(ctx, dom, pos)
@@ -477,15 +578,42 @@ def also_c3(reps=5):
         ev[3].record()
         torch.cuda.synchronize()
         ph += [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
-    (nx, ny, nz), ncells, reach = ab.ab_cell_shape(ctx, with_reach=True)
+    ph /= reps
     ab.ab_sync(ctx)
     ctx.close()
-    return {"workload": "16,777,216 points in 1024 Gaussian blobs, periodic cube, "
-                        f"r={w.radius:.7f} (64 neighbours mean): rebuild + gauss fwd + adjoint",
-            "pairs_per_step": pairs, "ms_per_step": ms,
-            "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True,
-            "phases_ms": {"build": ph[0] / reps, "fwd": ph[1] / reps, "bwd": ph[2] / reps},
-            "cells": [nx, ny, nz], "n_cells": ncells, "cell_split": list(reach)}
+    pk, pk_kind = peaks()
+    alu, alu_src = alu_peak(pk)
+    fwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_GAUSS_FWD
+    bwd_ops = cands * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR_GAUSS_BWD
+    import hashlib
+    src = os.path.join(ROOT, "paper_1704_08907_gb300", "csrc", "ab_pairs.cu")
+    same = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC_C3_SOURCE_SHA
+    bbytes = build_bytes(w.n, ncells // int(np.prod(reach)))   # width-r cells
+    out = {"workload": "16,777,216 points in 1024 Gaussian blobs, periodic cube, "
+                       f"r={w.radius:.7f} (64 neighbours mean): rebuild + gauss fwd + adjoint",
+           "pairs_per_step": pairs, "candidates_per_step": cands, "ms_per_step": ms,
+           "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True,
+           "phases_ms": {"build": ph[0], "fwd": ph[1], "bwd": ph[2]},
+           "cells": list(ncell), "n_cells": ncells, "cell_split": list(reach),
+           "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,GAUSS> (adjoint: x, w, s)",
+                        "achieved": bwd_ops / (ph[2] * 1e-3) / 1e12, "peak": alu, "unit": "Top/s",
+                        "frac": bwd_ops / (ph[2] * 1e-3) / 1e12 / alu,
+                        "traffic": TRAFFIC_C3_BWD_BYTES if same else None,
+                        "algorithmic_ops_per_launch": bwd_ops,
+                        "peak_source": alu_src,
+                        "timing": "the adjoint call's events: the kernel plus its two gathers"},
+           "fwd_alu_frac": fwd_ops / (ph[1] * 1e-3) / 1e12 / alu,
+           "build_hbm_frac": bbytes / (ph[0] * 1e-3) / 1e9 / pk["hbm_gbs"],
+           "build_bytes_algorithmic": bbytes}
+    nq = w.n // oracle_fraction
+    sp, t_cl, t_q, cores = oracle_sample_c3(w, nq)
+    full_s = t_cl + t_q * (w.n / nq)
+    out["cpu_baseline"] = {"value": pairs / full_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"oracle cell list over all {w.n} points ({t_cl:.2f} s) + "
+                                     f"Gaussian forward and adjoint for {nq} query particles "
+                                     f"({sp} pairs, {t_q:.2f} s), extrapolated linearly to all "
+                                     f"{w.n} particles"}
+    return out
 
 
 def also_md(loop_steps=200):
@@ -671,7 +799,7 @@ def also_sph(steps=50):
             "mean_density": float(rho.double().mean().item())}
 
 
-def also_bd(steps=100):
+def also_bd(steps=1000):
     """2-D Brownian dynamics, 4,194,304 particles, x periodic / y reflecting,
     soft repulsion within r = 0.002, Euler-Maruyama dt = 1e-5 with Philox
     noise, full cell-list rebuild every step (rebuild + force + step, all on

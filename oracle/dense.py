@@ -111,6 +111,50 @@ def grad_Y(X, Y, W, G, s, cols=None, block=256):
     return out
 
 
+def grad_X_abs(X, Y, W, G, s, rows=None, block=256):
+    """Per-element denominator of the dX error metric: the magnitudes of the
+    elementary terms of dL/dx_ik summed,
+
+        2 s sum_j sum_c |G_ic| |W_jc| K_ij |x_ik - y_jk|,
+
+    one term per (j, c) of dL/dx_ik = -2 s sum_j sum_c G_ic W_jc K_ij
+    (x_ik - y_jk).  It bounds |dL/dx_ik| and equals it when every term has
+    the same sign."""
+    X = _f64(X)
+    Y = _f64(Y)
+    W = np.abs(_f64(W))
+    G = np.abs(_f64(G))
+    if rows is not None:
+        X = X[np.asarray(rows)]
+        G = G[np.asarray(rows)]
+    out = np.zeros(X.shape)
+    for a in range(0, X.shape[0], block):
+        Xb = X[a:a + block]
+        B = (G[a:a + block] @ W.T) * kernel(Xb, Y, s)            # [b, n]
+        for k in range(X.shape[1]):
+            out[a:a + block, k] = 2.0 * s * (B * np.abs(Xb[:, k, None] - Y[None, :, k])).sum(1)
+    return out
+
+
+def grad_Y_abs(X, Y, W, G, s, cols=None, block=256):
+    """Per-element denominator of the dY error metric:
+    2 s sum_i sum_c |G_ic| |W_jc| K_ij |x_ik - y_jk| (see grad_X_abs)."""
+    X = _f64(X)
+    Y = _f64(Y)
+    W = np.abs(_f64(W))
+    G = np.abs(_f64(G))
+    if cols is not None:
+        Y = Y[np.asarray(cols)]
+        W = W[np.asarray(cols)]
+    out = np.zeros(Y.shape)
+    for a in range(0, X.shape[0], block):
+        Xb = X[a:a + block]
+        B = (G[a:a + block] @ W.T) * kernel(Xb, Y, s)            # [b, n]
+        for k in range(Y.shape[1]):
+            out[:, k] += 2.0 * s * (B * np.abs(Xb[:, k, None] - Y[None, :, k])).sum(0)
+    return out
+
+
 def grad_s(X, Y, W, G, s, block=256):
     """dL/ds = -sum_ij (G_i . W_j) K_ij d_ij^2 over all pairs."""
     X = _f64(X)
@@ -123,6 +167,12 @@ def grad_s(X, Y, W, G, s, block=256):
         A = (G[a:a + block] @ W.T) * np.exp(-s * D2)
         tot -= float((A * D2).sum())
     return tot
+
+
+def grad_s_abs(X, Y, W, G, s, block=256):
+    """Denominator of the ds error metric: sum_ij sum_c |G_ic| |W_jc| K_ij d_ij^2,
+    the magnitudes of the elementary terms of dL/ds summed."""
+    return -grad_s(X, Y, np.abs(_f64(W)), np.abs(_f64(G)), s, block)
 
 
 def grad_lengthscale(ds, lengthscale):

@@ -11,6 +11,7 @@ import torch
 import oracle
 import synth
 from _helpers import dev, host, oracle_box, rel_err
+from oracle import fd
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -151,7 +152,42 @@ def test_c3_full_gauss_fwd_bwd_sampled(ab, ctx):
     dp, dw, _ = oracle.abs_grad_terms("gauss", box, w.pos, off, idx, w.g, q, w=w.w, params=w.params)
     assert rel_err(host(gpos)[q, :3], rp[:, :3], dp[:, :3]) <= TOL
     assert rel_err(host(gw)[q], rw, dw) <= TOL
-    assert np.isfinite(float(gs))
+    assert np.isfinite(float(gs))   # ds over all pairs: test_c3_shaped_ds_all_pairs
+    # FP64 central differences of the loss on the same 4096 points (the
+    # clustered workload's stated check): no adjoint formula involved
+    fdp = fd.gauss_position_grad_fd(box, w.pos, off, idx, q, w.w, w.g, w.params["s"], h=1e-7)
+    assert rel_err(host(gpos)[q, :3], fdp, dp[:, :3]) <= TOL
+
+
+def test_c3_shaped_ds_all_pairs(ab, ctx):
+    """The lengthscale gradient ds sums over every pair, so its FP64 reference
+    needs all pairs: 262,144 points in 16 blobs of the clustered workload's
+    size (16,384 points, sd 0.01, the same radius, ~64 neighbours), the
+    adjoint (x, w, s) against the oracle on every particle, and ds against
+    FP64 central differences of the loss in s."""
+    w = synth.c3(n=1 << 18, n_blobs=16)
+    box, off, idx = _setup(ab, ctx, w, queries=np.arange(w.n))
+    prm = _params(ab, w)
+    gpos = torch.empty((w.n, 4), dtype=torch.float32, device="cuda:0")
+    gw = torch.empty(w.n, dtype=torch.float32, device="cuda:0")
+    gs = torch.empty((), dtype=torch.float64, device="cuda:0")
+    ab.ab_pair_sum_bwd(ctx, "gauss", prm, dev(w.w), dev(w.g), gpos, gw, gs)
+    rp, rw, rs = oracle.pair_grads("gauss", box, w.pos, off, idx, w.g, w=w.w, params=w.params)
+    dp, dw, ds = oracle.abs_grad_terms("gauss", box, w.pos, off, idx, w.g, w=w.w,
+                                       params=w.params)
+    assert rel_err(host(gpos)[:, :3], rp[:, :3], dp[:, :3]) <= TOL
+    assert rel_err(host(gw), rw, dw) <= TOL
+    e = abs(float(gs) - rs.sum()) / ds.sum()
+    assert e <= TOL, e
+    s0 = w.params["s"]
+    hs = 1e-6 * s0
+
+    def L(sv):
+        return float(w.g.astype(np.float64) @ oracle.pair_values(
+            "gauss", box, w.pos, off, idx, w=w.w, params={"s": sv})[:, 0])
+
+    fds = (L(s0 + hs) - L(s0 - hs)) / (2 * hs)
+    assert abs(float(gs) - fds) <= TOL * ds.sum()
 
 
 def test_paper_shape_expf_1m(ab, ctx):

@@ -82,3 +82,56 @@ def test_row_and_column_subsets():
     assert np.allclose(dense.matvec(w.X, w.Y, w.W, w.s, rows=rows), full[rows], rtol=1e-14)
     dW = dense.grad_W(w.X, w.Y, w.G, w.s)
     assert np.allclose(dense.grad_W(w.X, w.Y, w.G, w.s, cols=rows), dW[rows], rtol=1e-13)
+
+
+def test_adjoint_abs_terms_hand_computed():
+    """One x, two y, two right-hand sides: the elementary terms of dL/dx_ik
+    are -2 s G_ic W_jc K_j (x_k - y_jk), one per (j, c); the denominators sum
+    their magnitudes."""
+    X = np.array([[0.25, 0.5, 0.75]])
+    Y = np.array([[0.5, 0.25, 0.75], [0.0, 1.0, 0.5]])
+    W = np.array([[1.5, -0.5], [-2.0, 0.25]])
+    G = np.array([[0.5, -3.0]])
+    s = 2.0
+    K = [math.exp(-s * sum((X[0, k] - Y[j, k]) ** 2 for k in range(3))) for j in range(2)]
+    aX = [sum(2 * s * abs(G[0, c] * W[j, c]) * K[j] * abs(X[0, k] - Y[j, k])
+              for j in range(2) for c in range(2)) for k in range(3)]
+    vX = [sum(-2 * s * G[0, c] * W[j, c] * K[j] * (X[0, k] - Y[j, k])
+              for j in range(2) for c in range(2)) for k in range(3)]
+    assert np.allclose(dense.grad_X_abs(X, Y, W, G, s)[0], aX, rtol=1e-14)
+    assert np.allclose(dense.grad_X(X, Y, W, G, s)[0], vX, rtol=1e-13)
+    aY = [[sum(2 * s * abs(G[0, c] * W[j, c]) * K[j] * abs(X[0, k] - Y[j, k])
+               for c in range(2)) for k in range(3)] for j in range(2)]
+    assert np.allclose(dense.grad_Y_abs(X, Y, W, G, s), aY, rtol=1e-14)
+    aS = sum(abs(G[0, c] * W[j, c]) * K[j] * sum((X[0, k] - Y[j, k]) ** 2 for k in range(3))
+             for j in range(2) for c in range(2))
+    assert math.isclose(dense.grad_s_abs(X, Y, W, G, s), aS, rel_tol=1e-14)
+
+
+def test_adjoint_abs_terms_equal_magnitude_when_signs_agree():
+    """Positive G, W and every y below every x in each coordinate: all the
+    elementary terms of dX (and of dY) share one sign, so the denominator
+    equals |dX| (|dY|) exactly up to rounding."""
+    rng = np.random.default_rng(11)
+    X = 0.6 + 0.4 * rng.random((20, 3))
+    Y = 0.5 * rng.random((30, 3))
+    W = rng.random((30, 4)) + 0.1
+    G = rng.random((20, 4)) + 0.1
+    s = 3.0
+    assert np.allclose(dense.grad_X_abs(X, Y, W, G, s), np.abs(dense.grad_X(X, Y, W, G, s)),
+                       rtol=1e-12)
+    assert np.allclose(dense.grad_Y_abs(X, Y, W, G, s), np.abs(dense.grad_Y(X, Y, W, G, s)),
+                       rtol=1e-12)
+    assert math.isclose(dense.grad_s_abs(X, Y, W, G, s), abs(dense.grad_s(X, Y, W, G, s)),
+                        rel_tol=1e-12)
+
+
+def test_adjoint_abs_terms_bound_and_exceed_mixed_signs():
+    w = synth.c4(m=60, n=80, nrhs=8, seed_offset=4)
+    for fn, fa in ((dense.grad_X, dense.grad_X_abs), (dense.grad_Y, dense.grad_Y_abs)):
+        v = fn(w.X, w.Y, w.W, w.G, w.s)
+        a = fa(w.X, w.Y, w.W, w.G, w.s)
+        assert np.all(np.abs(v) <= a * (1 + 1e-12))
+        # signs of G, W and x - y are mixed: cancellation makes most
+        # elements strictly smaller than the sum of magnitudes
+        assert np.mean(np.abs(v) < 0.9 * a) > 0.5
