@@ -27,6 +27,24 @@ extern "C" {
 ab_status ab_testing_scan_timeout(ab_ctx* ctx, int64_t items, int32_t skip_tile,
                                   int64_t limit_ns);
 
+/* Select how the following ab_build calls run: single_launch = 1 (the
+ * default) builds the cell list in one cooperative launch whose phases are
+ * separated by bounded grid-wide barriers; 0 runs the same counting sort as
+ * a sequence of kernels.  Both give the same cell list bit for bit.
+ * Errors: AB_ERR_INVALID_ARG. */
+ab_status ab_testing_build_path(ab_ctx* ctx, int32_t single_launch);
+
+/* Make the next single-launch ab_build exercise its barrier timeout: block
+ * `skip_block` (clamped to none if the grid is smaller) never arrives at the
+ * first grid barrier, so every other block's wait there gives up after
+ * `limit_ns` nanoseconds (0 < limit_ns <= 2e9) and records AB_ERR_TIMEOUT in
+ * the context's error word; all later waits of that launch are bounded the
+ * same way, so the launch ends after at most five limits.  The cell list it
+ * leaves is garbage; the following ab_sync() returns AB_ERR_TIMEOUT and a
+ * new ab_build restores a valid cell list.  Applies to one build only.
+ * Errors: AB_ERR_INVALID_ARG. */
+ab_status ab_testing_build_timeout(ab_ctx* ctx, int32_t skip_block, int64_t limit_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -318,4 +318,14 @@ def ab_testing_scan_timeout(ctx: Context, items: int, skip_tile: int, limit_ns: 
                                         int(limit_ns)), ctx)
 
 
+def ab_testing_build_path(ctx: Context, single_launch: bool):
+    """Testing hook: one cooperative launch (True, default) or the kernel sequence."""
+    _check(_lib.ab_testing_build_path(ctx.handle, int(bool(single_launch))), ctx)
+
+
+def ab_testing_build_timeout(ctx: Context, skip_block: int, limit_ns: int):
+    """Testing hook: the next single-launch build's first barrier misses a block."""
+    _check(_lib.ab_testing_build_timeout(ctx.handle, int(skip_block), int(limit_ns)), ctx)
+
+
 from .autograd import GaussPairSum, KernelMatvec, LJEnergy, lj_energy_forces  # noqa: E402,F401

@@ -62,6 +62,7 @@ struct ab_ctx {
     cudaStream_t stream = nullptr;
     ab::CellList cl;
     ab::Scratch sc;
+    ab::BuildOptions build_opt;
     uint32_t* d_err = nullptr;
     std::string last_error;
 };
@@ -278,7 +279,7 @@ ab_status ab_destroy(ab_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_rank, c->cl.tmp,
                     c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
-                    c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws};
+                    c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws, c->sc.coop};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -357,9 +358,19 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
         return cuda_fail(c, e, "ab_build (cell table)");
     s = ensure_scan(c, g.n_cells + 1);
     if (s != AB_OK) return s;
+    if (!c->sc.coop) {
+        e = cudaMallocAsync((void**)&c->sc.coop, ab::coop_scratch_words() * sizeof(uint32_t), c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->sc.coop = nullptr;
+            return cuda_fail(c, e, "ab_build (build scratch)");
+        }
+    }
     cl.n = n;
     cl.g = g;
-    e = ab::launch_build(cl, pos, packed, c->sc, c->d_err, c->stream);
+    e = ab::launch_build(cl, pos, packed, c->sc, c->d_err, c->stream, c->build_opt);
+    c->build_opt.skip_block = -1;   // the timeout hook applies to one build only
+    c->build_opt.limit_ns = 0;
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_build launch");
     cl.user_pos = pos;
     cl.valid = true;
@@ -784,6 +795,19 @@ ab_status ab_md_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4, fl
 }
 
 // ---- testing hooks -------------------------------------------------------
+
+ab_status ab_testing_build_path(ab_ctx* c, int32_t single_launch) {
+    if (!c || (single_launch != 0 && single_launch != 1)) return AB_ERR_INVALID_ARG;
+    c->build_opt.single_launch = single_launch != 0;
+    return AB_OK;
+}
+
+ab_status ab_testing_build_timeout(ab_ctx* c, int32_t skip_block, int64_t limit_ns) {
+    if (!c || skip_block < 0 || limit_ns <= 0 || limit_ns > 2000000000ll) return AB_ERR_INVALID_ARG;
+    c->build_opt.skip_block = skip_block;
+    c->build_opt.limit_ns = (long long)limit_ns;
+    return AB_OK;
+}
 
 ab_status ab_testing_scan_timeout(ab_ctx* c, int64_t items, int32_t skip_tile,
                                   int64_t limit_ns) {

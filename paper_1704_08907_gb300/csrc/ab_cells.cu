@@ -285,6 +285,242 @@ k_reduce_partials(const double* __restrict__ partial, int count, double* __restr
     if (threadIdx.x == 0) *out = s[0];
 }
 
+
+// ---------------------------------------------------------------------------
+// The whole build in one cooperative launch: the same counting sort as the
+// kernels above (hash + histogram, exclusive scan, scatter, stable finalize),
+// phase after phase, separated by grid-wide barriers.  Every block is
+// resident (cooperative launch), each thread keeps several particles' loads
+// in flight, and no phase pays a launch.  Data written by other blocks during
+// the launch is read with ld.global.cg (L2), never through L1.
+// ---------------------------------------------------------------------------
+constexpr int kCoopThreads = 1024;
+constexpr int kCoopIlp = 4;             // particles per thread per loop trip
+constexpr int kCoopScanItems = 4;       // cells per thread per scan tile
+
+struct CoopArgs {
+    const float* pos;
+    int64_t n;
+    Geom g;
+    int64_t nc1;               // n_cells + 1 entries in cell_start
+    uint32_t* cell_start;      // counts, then offsets (in place)
+    uint2* cell_rank;          // per particle: (cell, arrival rank)
+    uint2* tmp;                // per unordered slot: (original index, cell)
+    uint32_t* perm;
+    float4* spos;
+    uint32_t* block_sum;       // [gridDim.x]
+    uint32_t* bar;             // [2]: arrivals, generation (zero at launch)
+    uint32_t* err;
+    long long limit_ns;
+    int skip_block;            // testing: this block never arrives at the first barrier (-1: none)
+};
+
+// Grid barrier: arrivals counted on bar[0], the last arrival resets it and
+// advances the generation bar[1].  The wait is bounded by a wall-clock limit;
+// a block that gives up latches DEVERR_SCAN_TIMEOUT and carries on (results
+// are then garbage, but every block still terminates).
+__device__ __forceinline__ void coop_barrier(uint32_t* bar, uint32_t* err, long long limit_ns,
+                                             bool absent = false) {
+    __syncthreads();
+    if (threadIdx.x == 0 && !absent) {
+        __threadfence();
+        const uint32_t gen = *((volatile uint32_t*)(bar + 1));
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = global_ns();
+            while (*((volatile uint32_t*)(bar + 1)) == gen) {
+                if (global_ns() - t0 > limit_ns) {
+                    atomicOr(err, DEVERR_SCAN_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t ldcg_u32(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint2 ldcg_u2(const uint2* p) { return __ldcg(p); }
+
+// Block-wide exclusive scan of one value per thread; returns the thread's
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        s_warp[lane] = x;   // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t before = warp ? s_warp[warp - 1] : 0u;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();    // s_warp is reused by the next call
+    return before + incl - v;
+}
+
+template <int DIM, bool PACKED>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+k_build_coop(CoopArgs a) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_red[32];
+    const int64_t n = a.n;
+    const int64_t tid = (int64_t)blockIdx.x * kCoopThreads + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * kCoopThreads;
+
+    // P0: zero the counts
+    for (int64_t c = tid; c < a.nc1; c += nthreads) a.cell_start[c] = 0u;
+    coop_barrier(a.bar, a.err, a.limit_ns, (int)blockIdx.x == a.skip_block);
+
+    // P1: cell hash + histogram; the atomic's return is the arrival rank
+    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
+        float4 p[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            p[u] = i < n ? load_pos<DIM, PACKED>(a.pos, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        uint32_t c[kCoopIlp], r[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            c[u] = (uint32_t)cell_coord(p[u].x, a.g.lo[0], a.g.inv_w[0], a.g.n[0]);
+            c[u] += (uint32_t)a.g.n[0] * (uint32_t)cell_coord(p[u].y, a.g.lo[1], a.g.inv_w[1], a.g.n[1]);
+            if (DIM == 3)
+                c[u] += (uint32_t)a.g.n[0] * (uint32_t)a.g.n[1] *
+                        (uint32_t)cell_coord(p[u].z, a.g.lo[2], a.g.inv_w[2], a.g.n[2]);
+        }
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            if (i0 + u * nthreads < n) r[u] = atomicAdd(a.cell_start + c[u], 1u);
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            if (i < n) a.cell_rank[i] = make_uint2(c[u], r[u]);
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P2a: each block sums its contiguous chunk of counts
+    const int64_t chunk = (a.nc1 + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = c0 + chunk < a.nc1 ? c0 + chunk : a.nc1;
+    {
+        uint32_t sum = 0;
+        for (int64_t c = c0 + threadIdx.x; c < c1; c += kCoopThreads) sum += ldcg_u32(a.cell_start + c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < kCoopThreads / 32; ++w) t += s_red[w];
+            a.block_sum[blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P2b: exclusive prefix of the earlier blocks' sums, then an in-place
+    // exclusive scan of the block's chunk in tiles
+    {
+        uint32_t pre = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kCoopThreads) pre += ldcg_u32(a.block_sum + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = pre;
+        __syncthreads();
+        uint32_t run = 0;
+        for (int w = 0; w < kCoopThreads / 32; ++w) run += s_red[w];
+        __syncthreads();
+        for (int64_t t0 = c0; t0 < c1; t0 += (int64_t)kCoopThreads * kCoopScanItems) {
+            const int64_t base = t0 + (int64_t)threadIdx.x * kCoopScanItems;
+            uint32_t v[kCoopScanItems];
+            uint32_t tsum = 0;
+#pragma unroll
+            for (int k = 0; k < kCoopScanItems; ++k) {
+                v[k] = base + k < c1 ? ldcg_u32(a.cell_start + base + k) : 0u;
+                tsum += v[k];
+            }
+            uint32_t total;
+            uint32_t ex = run + block_excl_scan(tsum, s_warp, &total);
+#pragma unroll
+            for (int k = 0; k < kCoopScanItems; ++k) {
+                if (base + k < c1) a.cell_start[base + k] = ex;
+                ex += v[k];
+            }
+            run += total;
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P3: scatter (original index, cell) into the particle's unordered slot
+    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
+        uint2 cr[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            cr[u] = i < n ? ldcg_u2(a.cell_rank + i) : make_uint2(0u, 0u);
+        }
+        uint32_t st[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            st[u] = i0 + u * nthreads < n ? ldcg_u32(a.cell_start + cr[u].x) : 0u;
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            if (i < n) a.tmp[st[u] + cr[u].y] = make_uint2((uint32_t)i, cr[u].x);
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P4: stable rank inside the cell (number of members with a smaller
+    // original index), then perm and the sorted positions
+    for (int64_t s0 = tid; s0 < n; s0 += nthreads * kCoopIlp) {
+        uint2 pc[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t s = s0 + u * nthreads;
+            pc[u] = s < n ? ldcg_u2(a.tmp + s) : make_uint2(0u, 0u);
+        }
+        uint32_t lo[kCoopIlp], hi[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const bool live = s0 + u * nthreads < n;
+            lo[u] = live ? ldcg_u32(a.cell_start + pc[u].y) : 0u;
+            hi[u] = live ? ldcg_u32(a.cell_start + pc[u].y + 1) : 0u;
+        }
+        float4 q[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            q[u] = s0 + u * nthreads < n ? load_pos<DIM, PACKED>(a.pos, pc[u].x)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            if (s0 + u * nthreads >= n) continue;
+            uint32_t r = 0;
+            for (uint32_t t = lo[u]; t < hi[u]; ++t) r += (__ldcg(&a.tmp[t].x) < pc[u].x) ? 1u : 0u;
+            const uint32_t d = lo[u] + r;
+            a.perm[d] = pc[u].x;
+            a.spos[d] = make_float4(q[u].x, q[u].y, DIM == 3 ? q[u].z : 0.0f, 0.0f);
+        }
+    }
+}
+
 }  // namespace
 
 size_t scan_tiles(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile); }
@@ -326,10 +562,58 @@ cudaError_t launch_reduce_partials(const double* partial, int count, double* out
     return cudaGetLastError();
 }
 
+// Grid of the cooperative build: every block resident (one 1024-thread block
+// per SM at most), and no more blocks than there is work for.
+static int coop_grid(const void* fn, int64_t n, int64_t nc1) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int64_t resident = (int64_t)per_sm * num_sms();
+    const int64_t work = n > nc1 ? n : nc1;
+    int64_t want = (work + (int64_t)kCoopThreads * kCoopIlp - 1) / ((int64_t)kCoopThreads * kCoopIlp);
+    if (want < 1) want = 1;
+    return (int)(want < resident ? want : resident);
+}
+
+size_t coop_scratch_words() { return 2 + 4096; }   // barrier words + block sums
+
 cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
-                         uint32_t* err, cudaStream_t st) {
+                         uint32_t* err, cudaStream_t st, const BuildOptions& opt) {
     const int64_t n = cl.n;
     const int64_t nc = cl.g.n_cells;
+    // one cooperative launch when the device allows it
+    if (sc.coop && opt.single_launch) {
+        const void* fn;
+        if (cl.g.dim == 3) fn = packed ? (const void*)k_build_coop<3, true> : (const void*)k_build_coop<3, false>;
+        else fn = packed ? (const void*)k_build_coop<2, true> : (const void*)k_build_coop<2, false>;
+        const int grid = coop_grid(fn, n, nc + 1);
+        if (grid >= 1 && grid <= 4096) {
+            CoopArgs a;
+            a.pos = pos;
+            a.n = n;
+            a.g = cl.g;
+            a.nc1 = nc + 1;
+            a.cell_start = cl.cell_start;
+            a.cell_rank = cl.cell_rank;
+            a.tmp = reinterpret_cast<uint2*>(cl.tmp);
+            a.perm = cl.perm;
+            a.spos = cl.spos;
+            a.bar = sc.coop;
+            a.block_sum = sc.coop + 2;
+            a.err = err;
+            a.limit_ns = opt.limit_ns > 0 ? opt.limit_ns : kScanLimitNs;
+            a.skip_block = opt.skip_block < grid ? opt.skip_block : -1;
+            cudaError_t e = cudaMemsetAsync(sc.coop, 0, 2 * sizeof(uint32_t), st);
+            if (e != cudaSuccess) return e;
+            void* args[] = {&a};
+            e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kCoopThreads), args, 0, st);
+            if (e == cudaSuccess) return cudaSuccess;
+            cudaGetLastError();   // not launchable here: fall back to the kernel sequence
+        }
+    }
     cudaError_t e = cudaMemsetAsync(cl.cell_start, 0, (size_t)(nc + 1) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     if (n > 0) {

@@ -74,13 +74,23 @@ struct Scratch {
     size_t cap_dense_ws = 0;
     uint8_t* solve_ws = nullptr;      // CG vectors and scalars
     size_t cap_solve_ws = 0;
+    uint32_t* coop = nullptr;         // cooperative build: barrier words + block sums
 };
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 
 // ab_cells.cu
+// How ab_build runs: one cooperative launch (default) or the kernel
+// sequence; the last two fields are testing hooks of the bounded barrier wait.
+struct BuildOptions {
+    bool single_launch = true;
+    int skip_block = -1;          // a block that never arrives at the first barrier
+    long long limit_ns = 0;       // barrier wait limit (0: one second)
+};
 AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
-                                   uint32_t* err, cudaStream_t st);
+                                   uint32_t* err, cudaStream_t st, const BuildOptions& opt);
+// words of Scratch::coop (allocated once per context)
+AB_HIDDEN size_t coop_scratch_words();
 AB_HIDDEN cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_scalar(const CellList& cl, const float* v, float* out,
                                            cudaStream_t st);

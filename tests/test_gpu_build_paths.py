@@ -1,0 +1,98 @@
+"""The cell-list build as one cooperative launch against the kernel sequence
+(GPU, C ABI): the same counting sort, so the same cell list bit for bit; and
+the single launch's bounded grid-barrier wait, made to run out without a
+fault or a hang."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _helpers import dev, host, oracle_box
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ab():
+    import paper_1704_08907_gb300 as ab
+    return ab
+
+
+@pytest.fixture(scope="module")
+def ctx(ab, cuda):
+    c = ab.Context(0)
+    yield c
+    ab.ab_testing_build_path(c, True)
+    c.close()
+
+
+def _case(name):
+    if name == "c2":
+        w = synth.c2()
+        return 3, (1, 1, 1), w.radius, w.pos
+    if name == "clustered":
+        w = synth.c3(n=1 << 18, n_blobs=16)
+        return 3, (1, 1, 1), w.radius, w.pos
+    if name == "2d_wall":
+        return 2, (1, 0), 0.002, synth.uniform_positions(300000, 2, 3)
+    if name == "one_cell":
+        pts = np.float32(0.25) + np.float32(1e-3) * synth.uniform_positions(3000, 3, 5)[:, :3]
+        return 3, (0, 0, 0), 0.3, synth.pack4(pts.astype(np.float32))
+    if name == "n1":
+        return 3, (1, 1, 1), 0.1, synth.uniform_positions(1, 3, 6)
+    return 2, (1, 1), 0.1, synth.uniform_positions(2, 2, 7)
+
+
+def _state(ab, ctx, dim, periodic, r, pos, single, packed=False):
+    ab.ab_testing_build_path(ctx, single)
+    dom = ab.Domain(dim, periodic, r)
+    p = dev(pos)
+    if packed:
+        p = dev(np.ascontiguousarray(pos[:, :dim]))
+    ab.ab_build(ctx, dom, p)
+    perm, start = ab.ab_cell_export(ctx)
+    cnt = ab.ab_pair_sum(ctx, "count", ab.OpParams())
+    ab.ab_sync(ctx)
+    return host(perm), host(start), host(cnt)
+
+
+@pytest.mark.parametrize("case", ["c2", "clustered", "2d_wall", "one_cell", "n1", "n2"])
+def test_single_launch_equals_kernel_sequence(ab, ctx, case):
+    dim, periodic, r, pos = _case(case)
+    a = _state(ab, ctx, dim, periodic, r, pos, True)
+    b = _state(ab, ctx, dim, periodic, r, pos, False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    # the sorted order is a permutation and the offsets end at n
+    assert np.array_equal(np.sort(a[0]), np.arange(len(pos)))
+    assert a[1][-1] == len(pos) and np.all(np.diff(a[1].astype(np.int64)) >= 0)
+
+
+def test_single_launch_packed_positions(ab, ctx):
+    w = synth.c2(n=200000)
+    a = _state(ab, ctx, 3, (1, 1, 1), 0.03, w.pos, True, packed=True)
+    b = _state(ab, ctx, 3, (1, 1, 1), 0.03, w.pos, False, packed=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_single_launch_barrier_timeout_reports_and_recovers(ab, ctx):
+    """Block 0 never arrives at the first grid barrier: the other blocks'
+    waits give up after 20 ms, the launch ends, ab_sync reports
+    AB_ERR_TIMEOUT, and the next build is correct again."""
+    ab.ab_testing_build_path(ctx, True)
+    w = synth.c1()
+    dom = ab.Domain(2, w.periodic, w.radius)
+    big = synth.uniform_positions(1 << 20, 2, 9)
+    ab.ab_testing_build_timeout(ctx, 0, 20_000_000)
+    ab.ab_build(ctx, ab.Domain(2, (1, 1), 0.002), dev(big))
+    with pytest.raises(ab.AbError) as e:
+        ab.ab_sync(ctx)
+    assert e.value.status == 6
+    ab.ab_sync(ctx)                                 # latch cleared
+    ab.ab_build(ctx, dom, dev(w.pos))
+    c = host(ab.ab_pair_sum(ctx, "count", ab.OpParams()))
+    off, _ = oracle.neighbours_brute(oracle_box(w), w.pos)
+    assert np.array_equal(c, np.diff(off).astype(np.float32))
+    ab.ab_sync(ctx)
