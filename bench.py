@@ -579,6 +579,29 @@ def also_c3(reps=5, oracle_fraction=64):
         torch.cuda.synchronize()
         ph += [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
     ph /= reps
+    # the same step with the forward and the adjoint in one walk (the
+    # upstream gradient is given, so the value and the gradient can be formed
+    # together; bit for bit the separate calls' outputs)
+    def step_vg():
+        ab.ab_build(ctx, dom, pos)
+        ab.ab_pair_sum_value_grad(ctx, "gauss", prm, wt, g, out=y, grad_pos4=gpos, grad_w=gw,
+                                  grad_s=gs)
+
+    for _ in range(2):
+        step_vg()
+    ms_vg = _timed(step_vg, reps)
+    ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    vg_ph = np.zeros(2)
+    for _ in range(reps):
+        ev2[0].record()
+        ab.ab_build(ctx, dom, pos)
+        ev2[1].record()
+        ab.ab_pair_sum_value_grad(ctx, "gauss", prm, wt, g, out=y, grad_pos4=gpos, grad_w=gw,
+                                  grad_s=gs)
+        ev2[2].record()
+        torch.cuda.synchronize()
+        vg_ph += [ev2[k].elapsed_time(ev2[k + 1]) for k in range(2)]
+    vg_ph /= reps
     ab.ab_sync(ctx)
     ctx.close()
     pk, pk_kind = peaks()
@@ -603,6 +626,14 @@ def also_c3(reps=5, oracle_fraction=64):
                         "peak_source": alu_src,
                         "timing": "the adjoint call's events: the kernel plus its two gathers"},
            "fwd_alu_frac": fwd_ops / (ph[1] * 1e-3) / 1e12 / alu,
+           "value_and_grad_step": {
+               "note": "rebuild + ab_pair_sum_value_grad: the forward values and the adjoint "
+                       "(x, w, s) in one walk over the pairs, bit for bit the separate calls",
+               "ms_per_step": ms_vg, "pairs_per_s": pairs / (ms_vg * 1e-3),
+               "phases_ms": {"build": vg_ph[0], "value_and_grad": vg_ph[1]},
+               "alu_frac": (cands * OPS_PER_CANDIDATE + pairs * (OPS_PER_PAIR_GAUSS_FWD +
+                                                                 OPS_PER_PAIR_GAUSS_BWD))
+                           / (vg_ph[1] * 1e-3) / 1e12 / alu},
            "build_hbm_frac": bbytes / (ph[0] * 1e-3) / 1e9 / pk["hbm_gbs"],
            "build_bytes_algorithmic": bbytes}
     nq = w.n // oracle_fraction

@@ -220,6 +220,26 @@ ab_status ab_pair_sum_bwd(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
                           const float* w, const float* grad_out,
                           float* grad_pos4, float* grad_w, double* grad_s);
 
+/* The forward of ab_pair_sum and its adjoint ab_pair_sum_bwd in one walk
+ * over the pairs, for a loss L = sum_i g_i y_i whose upstream gradient
+ * g = grad_out is known when the forward runs (a weighted sum of the
+ * outputs, or any step that needs the value and the gradient together).
+ * The pair terms and their derivatives share the predicate, the separation
+ * and the kernel value; every output is bit for bit that of ab_pair_sum
+ * followed by ab_pair_sum_bwd on the same cell list.
+ *   GAUSS: out = y (float32[n]); grad_pos4, grad_w, grad_s as
+ *          ab_pair_sum_bwd; energy unused.
+ *   LJ:    out = E_i (float32[n]); energy (device float64[1]) = sum_i E_i;
+ *          grad_pos4 as ab_pair_sum_bwd; grad_w, grad_s unused.
+ * w, grad_out as ab_pair_sum_bwd.  Every output is optional (NULL).
+ * Errors: AB_ERR_UNSUPPORTED (other operators), AB_ERR_ALIAS (an output
+ * overlaps an input or another output), AB_ERR_STALE, AB_ERR_INVALID_ARG,
+ * AB_ERR_OOM, AB_ERR_CUDA. */
+ab_status ab_pair_sum_value_grad(ab_ctx* ctx, ab_op op, const ab_op_params* prm,
+                                 const float* w, const float* grad_out, float* out,
+                                 double* energy, float* grad_pos4, float* grad_w,
+                                 double* grad_s);
+
 /* A pair energy and the gradient of its total in one walk over the pairs:
  * the loss is L = sum_i E_i, so every upstream gradient is 1 and the forward
  * and the adjoint can share the predicate and the powers of sig/d (the

@@ -192,6 +192,23 @@ def ab_pair_sum_bwd(ctx: Context, op, params, w, grad_out, grad_pos4=None, grad_
     return grad_pos4, grad_w, grad_s
 
 
+def ab_pair_sum_value_grad(ctx: Context, op, params, w, grad_out, out=None, energy=None,
+                           grad_pos4=None, grad_w=None, grad_s=None):
+    """Forward values and the adjoint for upstream gradient grad_out in one
+    walk (GAUSS, LJ); outputs as ab_pair_sum and ab_pair_sum_bwd."""
+    op = OPS.get(op, op)
+    for t, nm, dt in [(w, "w", torch.float32), (grad_out, "grad_out", torch.float32),
+                      (out, "out", torch.float32), (energy, "energy", torch.float64),
+                      (grad_pos4, "grad_pos4", torch.float32), (grad_w, "grad_w", torch.float32),
+                      (grad_s, "grad_s", torch.float64)]:
+        _dev(t, dt, None, nm)
+    ctx._stream()
+    _check(_lib.ab_pair_sum_value_grad(ctx.handle, op, ctypes.byref(params), _ptr(w),
+                                       _ptr(grad_out), _ptr(out), _ptr(energy), _ptr(grad_pos4),
+                                       _ptr(grad_w), _ptr(grad_s)), ctx)
+    return out, energy, grad_pos4, grad_w, grad_s
+
+
 def ab_pair_energy_grad(ctx: Context, op, params, E=None, grad_pos4=None, energy=None):
     """Energy and the gradient of the total energy in one walk (LJ):
     returns (E float32[n], dE_total/dx float32[n,4], total energy float64)."""

@@ -58,6 +58,8 @@ SIGNATURES = {
     "ab_pair_sum": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P]),
     "ab_pair_sum_bwd": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P,
                              P, P]),
+    "ab_pair_sum_value_grad": (ST, [P, ctypes.c_int, ctypes.POINTER(ab_op_params), P, P, P,
+                                    P, P, P, P]),
     "ab_pair_list": (ST, [P, P, P, I64, P]),
     "ab_kernel_matvec": (ST, [P, I64, I64, P, P, I32, P, F32, ctypes.c_int, P]),
     "ab_kernel_matvec_bwd": (ST, [P, I64, I64, P, P, I32, P, F32, ctypes.c_int, P,

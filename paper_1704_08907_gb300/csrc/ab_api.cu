@@ -515,9 +515,9 @@ ab_status ab_pair_energy_grad_packed(ab_ctx* c, ab_op op, const ab_op_params* pr
     return energy_grad_impl(c, op, prm, E, grad_pos, true, energy);
 }
 
-ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
-                          const float* grad_out, float* grad_pos4, float* grad_w,
-                          double* grad_s) {
+static ab_status pair_bwd_impl(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
+                               const float* grad_out, float* out, double* energy,
+                               float* grad_pos4, float* grad_w, double* grad_s, bool value) {
     if (!c) return AB_ERR_INVALID_ARG;
     ab_status s = require_cells(c);
     if (s != AB_OK) return s;
@@ -528,17 +528,20 @@ ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const fl
     if (n > 0 && !grad_out) return fail(c, AB_ERR_INVALID_ARG, "grad_out is NULL");
     if (op == AB_OP_GAUSS && n > 0 && !w) return fail(c, AB_ERR_INVALID_ARG, "GAUSS needs weights w");
     if (grad_pos4 && !aligned16(grad_pos4)) return fail(c, AB_ERR_INVALID_ARG, "grad_pos4 must be 16-byte aligned");
+    if (op != AB_OP_LJ) energy = nullptr;      // the LJ total only
     const size_t n4 = (size_t)n * 4, n16 = (size_t)n * 16;
     const void* ins[2] = {w, grad_out};
     const size_t inb[2] = {n4, n4};
-    for (int t = 0; t < 2; ++t) {
-        if (overlaps(grad_pos4, n16, ins[t], inb[t]) || overlaps(grad_w, n4, ins[t], inb[t]) ||
-            overlaps(grad_s, 8, ins[t], inb[t]))
-            return fail(c, AB_ERR_ALIAS, "an output overlaps an input");
+    const void* outs[5] = {grad_pos4, grad_w, grad_s, out, energy};
+    const size_t outb[5] = {n16, n4, 8, n4, 8};
+    for (int a = 0; a < 5; ++a) {
+        for (int t = 0; t < 2; ++t)
+            if (overlaps(outs[a], outb[a], ins[t], inb[t]))
+                return fail(c, AB_ERR_ALIAS, "an output overlaps an input");
+        for (int b = a + 1; b < 5; ++b)
+            if (overlaps(outs[a], outb[a], outs[b], outb[b]))
+                return fail(c, AB_ERR_ALIAS, "outputs overlap");
     }
-    if (overlaps(grad_pos4, n16, grad_w, n4) || overlaps(grad_s, 8, grad_pos4, n16) ||
-        overlaps(grad_s, 8, grad_w, n4))
-        return fail(c, AB_ERR_ALIAS, "outputs overlap");
     ab::DeviceGuard dg(c->device);
     if (!dg.ok) return fail(c, AB_ERR_CUDA, "cannot make device %d current", c->device);
     cudaError_t e;
@@ -547,25 +550,39 @@ ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const fl
     e = ab::launch_gather_w_pos(c->cl, grad_out, c->stream);
     if (e == cudaSuccess && op == AB_OP_GAUSS)
         e = ab::launch_gather_scalar(c->cl, w, reinterpret_cast<float*>(c->sc.sv), c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd gather");
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint gather");
     ab::PairOut o;
     o.grad_pos = (float4*)grad_pos4;
     o.grad_w = op == AB_OP_GAUSS ? grad_w : nullptr;
+    o.out = value ? out : nullptr;
     const int grid = ab::pair_grid(n);
-    const bool want_s = op == AB_OP_GAUSS && grad_s;
-    if (want_s) {
+    double* red = op == AB_OP_GAUSS ? grad_s : (value ? energy : nullptr);
+    if (red) {
         if ((s = ensure_partial(c, (size_t)grid)) != AB_OK) return s;
         o.partial = c->sc.partial;
         o.partial_count = grid;
     }
-    e = ab::launch_pair_bwd(c->cl, op, *prm, c->sc.sv, o, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd launch");
-    if (want_s) {
-        if (n > 0) e = ab::launch_reduce_partials(o.partial, grid, grad_s, c->stream);
-        else e = cudaMemsetAsync(grad_s, 0, sizeof(double), c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "ab_pair_sum_bwd ds");
+    e = ab::launch_pair_bwd(c->cl, op, *prm, c->sc.sv, o, c->stream, value);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
+    if (red) {
+        if (n > 0) e = ab::launch_reduce_partials(o.partial, grid, red, c->stream);
+        else e = cudaMemsetAsync(red, 0, sizeof(double), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "adjoint reduction");
     }
     return AB_OK;
+}
+
+ab_status ab_pair_sum_bwd(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
+                          const float* grad_out, float* grad_pos4, float* grad_w,
+                          double* grad_s) {
+    return pair_bwd_impl(c, op, prm, w, grad_out, nullptr, nullptr, grad_pos4, grad_w, grad_s,
+                         false);
+}
+
+ab_status ab_pair_sum_value_grad(ab_ctx* c, ab_op op, const ab_op_params* prm, const float* w,
+                                 const float* grad_out, float* out, double* energy,
+                                 float* grad_pos4, float* grad_w, double* grad_s) {
+    return pair_bwd_impl(c, op, prm, w, grad_out, out, energy, grad_pos4, grad_w, grad_s, true);
 }
 
 ab_status ab_pair_list(ab_ctx* c, int64_t* offsets, int32_t* idx, int64_t cap, int64_t* nnz) {

@@ -296,7 +296,7 @@ k_reduce_partials(const double* __restrict__ partial, int count, double* __restr
 // ---------------------------------------------------------------------------
 constexpr int kCoopThreads = 1024;
 constexpr int kCoopIlp = 4;             // particles per thread per loop trip
-constexpr int kCoopScanItems = 4;       // cells per thread per scan tile
+constexpr int kCoopScanItems = 16;      // cells per thread per scan tile (4 x 16-byte loads)
 
 struct CoopArgs {
     const float* pos;
@@ -415,13 +415,19 @@ k_build_coop(CoopArgs a) {
     }
     coop_barrier(a.bar, a.err, a.limit_ns);
 
-    // P2a: each block sums its contiguous chunk of counts
-    const int64_t chunk = (a.nc1 + gridDim.x - 1) / gridDim.x;
+    // P2a: each block sums its contiguous chunk of counts (chunks start on a
+    // 16-byte boundary)
+    const int64_t chunk = (((a.nc1 + gridDim.x - 1) / gridDim.x) + 3) & ~(int64_t)3;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
     const int64_t c1 = c0 + chunk < a.nc1 ? c0 + chunk : a.nc1;
     {
         uint32_t sum = 0;
-        for (int64_t c = c0 + threadIdx.x; c < c1; c += kCoopThreads) sum += ldcg_u32(a.cell_start + c);
+        int64_t c = c0 + (int64_t)threadIdx.x * 4;
+        for (; c + 4 <= c1; c += (int64_t)kCoopThreads * 4) {
+            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(a.cell_start + c));
+            sum += v.x + v.y + v.z + v.w;
+        }
+        for (; c < c1; ++c) sum += ldcg_u32(a.cell_start + c);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sum;
@@ -451,17 +457,41 @@ k_build_coop(CoopArgs a) {
             const int64_t base = t0 + (int64_t)threadIdx.x * kCoopScanItems;
             uint32_t v[kCoopScanItems];
             uint32_t tsum = 0;
+            const bool whole = base + kCoopScanItems <= c1;
+            if (whole) {
 #pragma unroll
-            for (int k = 0; k < kCoopScanItems; ++k) {
-                v[k] = base + k < c1 ? ldcg_u32(a.cell_start + base + k) : 0u;
-                tsum += v[k];
+                for (int q = 0; q < kCoopScanItems / 4; ++q) {
+                    const uint4 t = __ldcg(reinterpret_cast<const uint4*>(a.cell_start + base) + q);
+                    v[4 * q] = t.x;
+                    v[4 * q + 1] = t.y;
+                    v[4 * q + 2] = t.z;
+                    v[4 * q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kCoopScanItems; ++k)
+                    v[k] = base + k < c1 ? ldcg_u32(a.cell_start + base + k) : 0u;
             }
+#pragma unroll
+            for (int k = 0; k < kCoopScanItems; ++k) tsum += v[k];
             uint32_t total;
             uint32_t ex = run + block_excl_scan(tsum, s_warp, &total);
+            if (whole) {
 #pragma unroll
-            for (int k = 0; k < kCoopScanItems; ++k) {
-                if (base + k < c1) a.cell_start[base + k] = ex;
-                ex += v[k];
+                for (int q = 0; q < kCoopScanItems / 4; ++q) {
+                    uint4 t;
+                    t.x = ex; ex += v[4 * q];
+                    t.y = ex; ex += v[4 * q + 1];
+                    t.z = ex; ex += v[4 * q + 2];
+                    t.w = ex; ex += v[4 * q + 3];
+                    reinterpret_cast<uint4*>(a.cell_start + base)[q] = t;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kCoopScanItems; ++k) {
+                    if (base + k < c1) a.cell_start[base + k] = ex;
+                    ex += v[k];
+                }
             }
             run += total;
         }

@@ -127,9 +127,11 @@ AB_HIDDEN int num_sms();   // SM count of the current device
 AB_HIDDEN cudaError_t launch_pair_fwd(const CellList& cl, ab_op op,
                                       const ab_op_params& prm, const float2* sv,
                                       PairOut& o, cudaStream_t st);
+// value: also the forward values (o.out) in the same walk; LJ energy
+// partials then go to o.partial
 AB_HIDDEN cudaError_t launch_pair_bwd(const CellList& cl, ab_op op,
                                       const ab_op_params& prm, const float2* sv,
-                                      PairOut& o, cudaStream_t st);
+                                      PairOut& o, cudaStream_t st, bool value = false);
 // LJ energy + gradient of the total energy in one walk (PairOut out, grad_pos,
 // partial)
 AB_HIDDEN cudaError_t launch_pair_energy_grad(const CellList& cl, ab_op op,

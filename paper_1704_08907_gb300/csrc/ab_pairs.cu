@@ -310,7 +310,7 @@ k_pair_fwd(PairParams P, PairOut o) {
             if (OP == AB_OP_COUNT) {
                 a0 += 1.0f;
             } else if (OP == AB_OP_GAUSS) {
-                a0 += pj.w * ex2_approx(-P.s_log2e * d2);
+                a0 = fmaf(pj.w, ex2_approx(-P.s_log2e * d2), a0);
             } else {   // SPH_DENSITY: m_j W(d)
                 float q;
                 const float t = wend_t(d2, P.inv_r, q);
@@ -381,7 +381,12 @@ k_pair_fwd_q(PairParams P, PairOut o) {
 // Adjoints (GAUSS, LJ): direct visit.  (A batched variant that collected
 // acceptances in a per-lane bit mask and evaluated the bodies when draining
 // it measured 6-15% slower once the predicate was packed.)
-template <int DIM, bool GENERAL, int OP>
+// VALUE: the forward value of the same operator in the same walk (the
+// upstream gradient is known when the forward runs); each forward term is
+// the forward kernel's expression, accumulated in the same visit order, so
+// both outputs equal the separate kernels' bit for bit.  With VALUE the
+// partials carry the LJ energy (GAUSS: still ds).
+template <int DIM, bool GENERAL, int OP, bool VALUE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_bwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
@@ -391,12 +396,13 @@ k_pair_bwd(PairParams P, PairOut o) {
     // positions; GAUSS also needs w, a float per particle (sv as float[n])
     const float* __restrict__ wv = reinterpret_cast<const float*>(P.sv);
     const float wi = (live && OP == AB_OP_GAUSS) ? __ldg(wv + s) : 0.0f;
-    float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f;
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f, y = 0.0f;
     if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
         [&](uint32_t j, const float4& pj, float dx, float dy, float dz, float d2) {
             if (OP == AB_OP_GAUSS) {
                 const float wj = __ldg(wv + j);
                 const float k = ex2_approx(-P.s_log2e * d2);
+                if (VALUE) y = fmaf(wj, k, y);
                 const float coef = fmaf(pi.w, wj, pj.w * wi) * k;
                 gx = fmaf(coef, dx, gx);
                 gy = fmaf(coef, dy, gy);
@@ -407,14 +413,17 @@ k_pair_bwd(PairParams P, PairOut o) {
                 const float inv = rcp_approx(d2);
                 const float sr2 = P.sig2 * inv;
                 const float sr6 = sr2 * sr2 * sr2;
+                if (VALUE) y = fmaf(sr6, sr6 - 1.0f, y);
                 const float coef = (pi.w + pj.w) * (sr6 * fmaf(6.0f, sr6, -3.0f)) * inv;
                 gx = fmaf(coef, dx, gx);
                 gy = fmaf(coef, dy, gy);
                 gz = fmaf(coef, dz, gz);
             }
         });
+    if (VALUE && OP == AB_OP_LJ) y *= 0.5f * P.eps;
     if (live) {
         const uint32_t p = __ldg(P.perm + s);
+        if (VALUE && o.out) o.out[p] = y;
         if (OP == AB_OP_GAUSS) {
             const float two_s = 2.0f * P.s;
             if (o.grad_pos)
@@ -427,6 +436,8 @@ k_pair_bwd(PairParams P, PairOut o) {
     }
     if (OP == AB_OP_GAUSS && o.partial)
         block_partial<kPairThreads>(live ? -(double)pi.w * (double)ds : 0.0, o.partial);
+    if (VALUE && OP == AB_OP_LJ && o.partial)
+        block_partial<kPairThreads>(live ? (double)y : 0.0, o.partial);
 }
 
 // LJ energy and its gradient in one walk, for a loss equal to the total
@@ -562,12 +573,18 @@ cudaError_t launch_pair_fwd(const CellList& cl, ab_op op, const ab_op_params& pr
 }
 
 cudaError_t launch_pair_bwd(const CellList& cl, ab_op op, const ab_op_params& prm,
-                            const float2* sv, PairOut& o, cudaStream_t st) {
+                            const float2* sv, PairOut& o, cudaStream_t st, bool value) {
     if (cl.n <= 0) return cudaSuccess;
     PairParams P = make_params(cl, prm, sv);
     switch (op) {
-        case AB_OP_GAUSS: AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_GAUSS), P, o); break;
-        case AB_OP_LJ: AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_LJ), P, o); break;
+        case AB_OP_GAUSS:
+            if (value) AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_GAUSS) COMMA_OP(true), P, o);
+            else AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_GAUSS) COMMA_OP(false), P, o);
+            break;
+        case AB_OP_LJ:
+            if (value) AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_LJ) COMMA_OP(true), P, o);
+            else AB_DISPATCH_DG(k_pair_bwd, kPairThreads, COMMA_OP(AB_OP_LJ) COMMA_OP(false), P, o);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
