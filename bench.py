@@ -924,18 +924,20 @@ def probe(spec):
     import torch
     import paper_1704_08907_gb300 as ab
     kind, _, items = spec.partition(":")
-    if kind == "c3":   # one rebuild + Gaussian forward + adjoint on the clustered 16.7M points
+    if kind == "c3":   # one rebuild + Gaussian forward + adjoint + value-and-gradient, clustered 16.7M
         w = synth.c3()
         ctx = ab.Context(0)
         dom = ab.Domain(3, w.periodic, w.radius)
         ab.ab_build(ctx, dom, torch.from_numpy(w.pos).cuda())
         wt, g = torch.from_numpy(w.w).cuda(), torch.from_numpy(w.g).cuda()
         prm = ab.OpParams(s=w.params["s"])
-        ab.ab_pair_sum(ctx, "gauss", prm, w=wt)
-        ab.ab_pair_sum_bwd(ctx, "gauss", prm, wt, g,
-                           torch.empty((w.n, 4), dtype=torch.float32, device="cuda"),
-                           torch.empty(w.n, dtype=torch.float32, device="cuda"),
-                           torch.empty((), dtype=torch.float64, device="cuda"))
+        y = ab.ab_pair_sum(ctx, "gauss", prm, w=wt)
+        gp = torch.empty((w.n, 4), dtype=torch.float32, device="cuda")
+        gw = torch.empty(w.n, dtype=torch.float32, device="cuda")
+        gs = torch.empty((), dtype=torch.float64, device="cuda")
+        ab.ab_pair_sum_bwd(ctx, "gauss", prm, wt, g, gp, gw, gs)
+        ab.ab_pair_sum_value_grad(ctx, "gauss", prm, wt, g, out=y, grad_pos4=gp, grad_w=gw,
+                                  grad_s=gs)
         ab.ab_sync(ctx)
         torch.cuda.synchronize()
         ctx.close()

@@ -145,7 +145,14 @@ ab_status ab_sync(ab_ctx* ctx);
  * into kx = 2..4 parts (see ab_cell_shape).  Steps: cell hash + histogram, exclusive scan
  * of the counts (cell offsets), stable counting-sort scatter of the
  * positions.  The sort is stable: within a cell, particles keep ascending
- * original index, so every later result is deterministic.
+ * original index, so every later result is deterministic.  When the lattice
+ * has more than 4 cells a particle (clustered inputs leave most cells
+ * empty), the library keeps offsets of the occupied cells only, with a
+ * bitmap of occupied cells to find them (about 0.25 bytes a cell plus 4 a
+ * particle instead of 4 bytes a cell); the order and every result are the
+ * same bit for bit.  The build runs as one cooperative launch whose phases
+ * are separated by grid barriers with bounded waits (a wait that gives up is
+ * reported by ab_sync as AB_ERR_TIMEOUT).
  *   dom:  host pointer to the domain (copied).
  *   n:    number of particles, 0 <= n < 2^31.
  *   pos4: float32[n][4] device positions (16-byte aligned).
@@ -177,7 +184,8 @@ ab_status ab_cell_shape(ab_ctx* ctx, int32_t* ncell, int64_t* n_cells,
 /* Copy out the last cell list for inspection: perm (device uint32[n],
  * perm[s] = original index of sorted slot s) and cell_start (device
  * uint32[n_cells + 1], particles of cell c occupy slots
- * [cell_start[c], cell_start[c+1])).  Either pointer may be NULL. */
+ * [cell_start[c], cell_start[c+1]); a compact table is expanded to every
+ * cell).  Either pointer may be NULL. */
 ab_status ab_cell_export(ab_ctx* ctx, uint32_t* perm, uint32_t* cell_start);
 
 /* Fixed-radius pair sum over the last cell list (Sec. 2.2.2 box search over

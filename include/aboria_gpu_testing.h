@@ -27,10 +27,19 @@ extern "C" {
 ab_status ab_testing_scan_timeout(ab_ctx* ctx, int64_t items, int32_t skip_tile,
                                   int64_t limit_ns);
 
+/* Select the cell table of the following ab_build calls: mode 0 (the
+ * default) keeps offsets of the occupied cells only when the lattice has
+ * more than 4 cells a particle, 1 always keeps the dense table of every
+ * cell, 2 always keeps the compact one (except on the general path, which
+ * is always dense).  Every result is the same bit for bit; only memory and
+ * time differ.  Errors: AB_ERR_INVALID_ARG. */
+ab_status ab_testing_cell_table(ab_ctx* ctx, int32_t mode);
+
 /* Select how the following ab_build calls run: single_launch = 1 (the
  * default) builds the cell list in one cooperative launch whose phases are
  * separated by bounded grid-wide barriers; 0 runs the same counting sort as
- * a sequence of kernels.  Both give the same cell list bit for bit.
+ * a sequence of kernels (a compact table is always built in one launch).
+ * Both give the same cell list bit for bit.
  * Errors: AB_ERR_INVALID_ARG. */
 ab_status ab_testing_build_path(ab_ctx* ctx, int32_t single_launch);
 

@@ -335,6 +335,11 @@ def ab_testing_scan_timeout(ctx: Context, items: int, skip_tile: int, limit_ns: 
                                         int(limit_ns)), ctx)
 
 
+def ab_testing_cell_table(ctx: Context, mode: int):
+    """Testing hook: 0 automatic, 1 dense table, 2 table of occupied cells."""
+    _check(_lib.ab_testing_cell_table(ctx.handle, int(mode)), ctx)
+
+
 def ab_testing_build_path(ctx: Context, single_launch: bool):
     """Testing hook: one cooperative launch (True, default) or the kernel sequence."""
     _check(_lib.ab_testing_build_path(ctx.handle, int(bool(single_launch))), ctx)

@@ -74,6 +74,7 @@ SIGNATURES = {
     "ab_last_error": (ctypes.c_char_p, [P]),
     "ab_testing_scan_timeout": (ST, [P, I64, I32, I64]),
     "ab_testing_build_path": (ST, [P, I32]),
+    "ab_testing_cell_table": (ST, [P, I32]),
     "ab_testing_build_timeout": (ST, [P, I32, I64]),
     "ab_exclusive_scan_u32_static": (ST, [P, P, I64, P]),
 }

@@ -63,6 +63,8 @@ struct ab_ctx {
     ab::CellList cl;
     ab::Scratch sc;
     ab::BuildOptions build_opt;
+    int coop_launch = 0;      // the device supports cooperative launches
+    int table_mode = 0;       // testing: 0 automatic, 1 dense, 2 compact where allowed
     uint32_t* d_err = nullptr;
     std::string last_error;
 };
@@ -263,6 +265,10 @@ ab_status ab_create(ab_ctx** out, int device, void* stream) {
     ab_ctx* c = new ab_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    if (cudaDeviceGetAttribute(&c->coop_launch, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) {
+        cudaGetLastError();
+        c->coop_launch = 0;
+    }
     if (cudaMalloc((void**)&c->d_err, 16) != cudaSuccess ||
         cudaMemset(c->d_err, 0, 16) != cudaSuccess) {
         cudaGetLastError();
@@ -278,7 +284,7 @@ ab_status ab_destroy(ab_ctx* c) {
     ab::DeviceGuard dg(c->device);
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_rank, c->cl.tmp,
-                    c->cl.cell_start, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
+                    c->cl.cell_start, c->cl.occ, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
                     c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws, c->sc.coop};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
@@ -329,6 +335,13 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
     CellList& cl = c->cl;
     cl.valid = false;
     Geom g = make_geom(dom, n);
+    // clustered inputs leave most cells empty: above 4 cells a particle the
+    // table keeps offsets of the occupied cells only (needs the single-launch
+    // build; the general path keeps the dense table)
+    g.compact = 0;
+    if (!g.general && c->coop_launch && c->table_mode != 1 &&
+        (c->table_mode == 2 || g.n_cells > 4 * (n > 0 ? n : 1)))
+        g.compact = 1;
     const size_t nn = (size_t)(n > 0 ? n : 1);
     cudaError_t e;
     if (nn > cl.cap_n || !cl.spos) {
@@ -354,8 +367,12 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
         cl.tmp = (uint32_t*)fresh[3];
         cl.cap_n = want;
     }
-    if ((e = grow(&cl.cell_start, &cl.cap_cells, (size_t)g.n_cells + 1, c->stream)) != cudaSuccess)
+    const size_t table = g.compact ? (size_t)n + 1 : (size_t)g.n_cells + 1;
+    if ((e = grow(&cl.cell_start, &cl.cap_cells, table, c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ab_build (cell table)");
+    if (g.compact &&
+        (e = grow(&cl.occ, &cl.cap_occ, (size_t)ab::occ_words(g.n_cells), c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ab_build (occupancy table)");
     s = ensure_scan(c, g.n_cells + 1);
     if (s != AB_OK) return s;
     if (!c->sc.coop) {
@@ -409,9 +426,13 @@ ab_status ab_cell_export(ab_ctx* c, uint32_t* perm, uint32_t* cell_start) {
     cudaError_t e = cudaSuccess;
     if (perm && c->cl.n > 0)
         e = cudaMemcpyAsync(perm, c->cl.perm, (size_t)c->cl.n * 4, cudaMemcpyDeviceToDevice, c->stream);
-    if (e == cudaSuccess && cell_start)
-        e = cudaMemcpyAsync(cell_start, c->cl.cell_start, (size_t)(c->cl.g.n_cells + 1) * 4,
-                            cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && cell_start) {
+        if (c->cl.g.compact)
+            e = ab::launch_expand_cells(c->cl, cell_start, c->stream);
+        else
+            e = cudaMemcpyAsync(cell_start, c->cl.cell_start, (size_t)(c->cl.g.n_cells + 1) * 4,
+                                cudaMemcpyDeviceToDevice, c->stream);
+    }
     return e == cudaSuccess ? AB_OK : cuda_fail(c, e, "ab_cell_export");
 }
 
@@ -812,6 +833,12 @@ ab_status ab_md_step(ab_ctx* c, const ab_domain* dom, int64_t n, float* pos4, fl
 }
 
 // ---- testing hooks -------------------------------------------------------
+
+ab_status ab_testing_cell_table(ab_ctx* c, int32_t mode) {
+    if (!c || mode < 0 || mode > 2) return AB_ERR_INVALID_ARG;
+    c->table_mode = mode;
+    return AB_OK;
+}
 
 ab_status ab_testing_build_path(ab_ctx* c, int32_t single_launch) {
     if (!c || (single_launch != 0 && single_launch != 1)) return AB_ERR_INVALID_ARG;

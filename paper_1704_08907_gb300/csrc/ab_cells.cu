@@ -293,6 +293,14 @@ k_reduce_partials(const double* __restrict__ partial, int count, double* __restr
 // resident (cooperative launch), each thread keeps several particles' loads
 // in flight, and no phase pays a launch.  Data written by other blocks during
 // the launch is read with ld.global.cg (L2), never through L1.
+//
+// Compact variant (clustered inputs, many more cells than particles): the
+// table holds offsets of the occupied cells only.  The hash marks each
+// particle's cell in an occupancy bitmap (64 cells a word, with the number of
+// occupied cells before the word beside it); the histogram, scan, scatter and
+// finalize then run over the compact index of the cell (its rank among the
+// occupied cells), which orders particles exactly as the cell id does, so the
+// sorted order is the dense table's bit for bit.
 // ---------------------------------------------------------------------------
 constexpr int kCoopThreads = 1024;
 constexpr int kCoopIlp = 4;             // particles per thread per loop trip
@@ -302,10 +310,12 @@ struct CoopArgs {
     const float* pos;
     int64_t n;
     Geom g;
-    int64_t nc1;               // n_cells + 1 entries in cell_start
-    uint32_t* cell_start;      // counts, then offsets (in place)
-    uint2* cell_rank;          // per particle: (cell, arrival rank)
-    uint2* tmp;                // per unordered slot: (original index, cell)
+    int64_t nc1;               // n_cells + 1 entries in cell_start (dense)
+    uint32_t* cell_start;      // counts, then offsets (in place); compact: per occupied cell
+    uint4* occ;                // compact: occupancy words
+    int64_t n_words;           // compact: occ_words(n_cells)
+    uint2* cell_rank;          // per particle: (cell or compact index, arrival rank)
+    uint2* tmp;                // per unordered slot: (original index, cell or compact index)
     uint32_t* perm;
     float4* spos;
     uint32_t* block_sum;       // [gridDim.x]
@@ -374,131 +384,104 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
     return before + incl - v;
 }
 
-template <int DIM, bool PACKED>
-__global__ void __launch_bounds__(kCoopThreads, 1)
-k_build_coop(CoopArgs a) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_red[32];
-    const int64_t n = a.n;
-    const int64_t tid = (int64_t)blockIdx.x * kCoopThreads + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * kCoopThreads;
+// Sum of one value per thread over the block (every thread gets it).
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* s_red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int w = 0; w < kCoopThreads / 32; ++w) t += s_red[w];
+    __syncthreads();
+    return t;
+}
 
-    // P0: zero the counts
-    for (int64_t c = tid; c < a.nc1; c += nthreads) a.cell_start[c] = 0u;
-    coop_barrier(a.bar, a.err, a.limit_ns, (int)blockIdx.x == a.skip_block);
+// Exclusive prefix of the sums of the blocks before this one.
+__device__ __forceinline__ uint32_t earlier_blocks(const uint32_t* block_sum, uint32_t* s_red) {
+    uint32_t pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kCoopThreads) pre += ldcg_u32(block_sum + b);
+    return block_sum_u32(pre, s_red);
+}
 
-    // P1: cell hash + histogram; the atomic's return is the arrival rank
-    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
-        float4 p[kCoopIlp];
-#pragma unroll
-        for (int u = 0; u < kCoopIlp; ++u) {
-            const int64_t i = i0 + u * nthreads;
-            p[u] = i < n ? load_pos<DIM, PACKED>(a.pos, i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        uint32_t c[kCoopIlp], r[kCoopIlp];
-#pragma unroll
-        for (int u = 0; u < kCoopIlp; ++u) {
-            c[u] = (uint32_t)cell_coord(p[u].x, a.g.lo[0], a.g.inv_w[0], a.g.n[0]);
-            c[u] += (uint32_t)a.g.n[0] * (uint32_t)cell_coord(p[u].y, a.g.lo[1], a.g.inv_w[1], a.g.n[1]);
-            if (DIM == 3)
-                c[u] += (uint32_t)a.g.n[0] * (uint32_t)a.g.n[1] *
-                        (uint32_t)cell_coord(p[u].z, a.g.lo[2], a.g.inv_w[2], a.g.n[2]);
-        }
-#pragma unroll
-        for (int u = 0; u < kCoopIlp; ++u)
-            if (i0 + u * nthreads < n) r[u] = atomicAdd(a.cell_start + c[u], 1u);
-#pragma unroll
-        for (int u = 0; u < kCoopIlp; ++u) {
-            const int64_t i = i0 + u * nthreads;
-            if (i < n) a.cell_rank[i] = make_uint2(c[u], r[u]);
-        }
-    }
-    coop_barrier(a.bar, a.err, a.limit_ns);
-
-    // P2a: each block sums its contiguous chunk of counts (chunks start on a
-    // 16-byte boundary)
-    const int64_t chunk = (((a.nc1 + gridDim.x - 1) / gridDim.x) + 3) & ~(int64_t)3;
+// In-place exclusive scan of arr[0 .. len) by the whole grid: each block
+// sums a contiguous chunk (16-byte aligned), a grid barrier, then each block
+// scans its chunk in tiles behind the sums of the earlier blocks.
+__device__ void coop_scan_u32(uint32_t* arr, int64_t len, const CoopArgs& a, uint32_t* s_warp,
+                              uint32_t* s_red) {
+    const int64_t chunk = (((len + gridDim.x - 1) / gridDim.x) + 3) & ~(int64_t)3;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
-    const int64_t c1 = c0 + chunk < a.nc1 ? c0 + chunk : a.nc1;
+    const int64_t c1 = c0 + chunk < len ? c0 + chunk : len;
     {
         uint32_t sum = 0;
         int64_t c = c0 + (int64_t)threadIdx.x * 4;
         for (; c + 4 <= c1; c += (int64_t)kCoopThreads * 4) {
-            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(a.cell_start + c));
+            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(arr + c));
             sum += v.x + v.y + v.z + v.w;
         }
-        for (; c < c1; ++c) sum += ldcg_u32(a.cell_start + c);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sum;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t t = 0;
-            for (int w = 0; w < kCoopThreads / 32; ++w) t += s_red[w];
-            a.block_sum[blockIdx.x] = t;
-        }
-        __syncthreads();
+        for (; c < c1; ++c) sum += ldcg_u32(arr + c);   // at most one thread's tail of < 4
+        const uint32_t t = block_sum_u32(sum, s_red);
+        if (threadIdx.x == 0) a.block_sum[blockIdx.x] = t;
     }
     coop_barrier(a.bar, a.err, a.limit_ns);
-
-    // P2b: exclusive prefix of the earlier blocks' sums, then an in-place
-    // exclusive scan of the block's chunk in tiles
-    {
-        uint32_t pre = 0;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kCoopThreads) pre += ldcg_u32(a.block_sum + b);
+    uint32_t run = earlier_blocks(a.block_sum, s_red);
+    for (int64_t t0 = c0; t0 < c1; t0 += (int64_t)kCoopThreads * kCoopScanItems) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * kCoopScanItems;
+        uint32_t v[kCoopScanItems];
+        const bool whole = base + kCoopScanItems <= c1;
+        if (whole) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = pre;
-        __syncthreads();
-        uint32_t run = 0;
-        for (int w = 0; w < kCoopThreads / 32; ++w) run += s_red[w];
-        __syncthreads();
-        for (int64_t t0 = c0; t0 < c1; t0 += (int64_t)kCoopThreads * kCoopScanItems) {
-            const int64_t base = t0 + (int64_t)threadIdx.x * kCoopScanItems;
-            uint32_t v[kCoopScanItems];
-            uint32_t tsum = 0;
-            const bool whole = base + kCoopScanItems <= c1;
-            if (whole) {
-#pragma unroll
-                for (int q = 0; q < kCoopScanItems / 4; ++q) {
-                    const uint4 t = __ldcg(reinterpret_cast<const uint4*>(a.cell_start + base) + q);
-                    v[4 * q] = t.x;
-                    v[4 * q + 1] = t.y;
-                    v[4 * q + 2] = t.z;
-                    v[4 * q + 3] = t.w;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kCoopScanItems; ++k)
-                    v[k] = base + k < c1 ? ldcg_u32(a.cell_start + base + k) : 0u;
+            for (int q = 0; q < kCoopScanItems / 4; ++q) {
+                const uint4 t = __ldcg(reinterpret_cast<const uint4*>(arr + base) + q);
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
             }
+        } else {
 #pragma unroll
-            for (int k = 0; k < kCoopScanItems; ++k) tsum += v[k];
-            uint32_t total;
-            uint32_t ex = run + block_excl_scan(tsum, s_warp, &total);
-            if (whole) {
-#pragma unroll
-                for (int q = 0; q < kCoopScanItems / 4; ++q) {
-                    uint4 t;
-                    t.x = ex; ex += v[4 * q];
-                    t.y = ex; ex += v[4 * q + 1];
-                    t.z = ex; ex += v[4 * q + 2];
-                    t.w = ex; ex += v[4 * q + 3];
-                    reinterpret_cast<uint4*>(a.cell_start + base)[q] = t;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kCoopScanItems; ++k) {
-                    if (base + k < c1) a.cell_start[base + k] = ex;
-                    ex += v[k];
-                }
-            }
-            run += total;
+            for (int k = 0; k < kCoopScanItems; ++k) v[k] = base + k < c1 ? ldcg_u32(arr + base + k) : 0u;
         }
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kCoopScanItems; ++k) tsum += v[k];
+        uint32_t total;
+        uint32_t ex = run + block_excl_scan(tsum, s_warp, &total);
+        if (whole) {
+#pragma unroll
+            for (int q = 0; q < kCoopScanItems / 4; ++q) {
+                uint4 t;
+                t.x = ex; ex += v[4 * q];
+                t.y = ex; ex += v[4 * q + 1];
+                t.z = ex; ex += v[4 * q + 2];
+                t.w = ex; ex += v[4 * q + 3];
+                reinterpret_cast<uint4*>(arr + base)[q] = t;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCoopScanItems; ++k) {
+                if (base + k < c1) arr[base + k] = ex;
+                ex += v[k];
+            }
+        }
+        run += total;
     }
-    coop_barrier(a.bar, a.err, a.limit_ns);
+}
 
-    // P3: scatter (original index, cell) into the particle's unordered slot
+// The cell index of every particle (dense: the cell id; with occ: its rank
+// among the occupied cells) -- the hash of the kernel sequence.
+template <int DIM, bool PACKED>
+__device__ __forceinline__ uint32_t particle_cell(const CoopArgs& a, const float4& p) {
+    uint32_t c = (uint32_t)cell_coord(p.x, a.g.lo[0], a.g.inv_w[0], a.g.n[0]);
+    c += (uint32_t)a.g.n[0] * (uint32_t)cell_coord(p.y, a.g.lo[1], a.g.inv_w[1], a.g.n[1]);
+    if (DIM == 3)
+        c += (uint32_t)a.g.n[0] * (uint32_t)a.g.n[1] *
+             (uint32_t)cell_coord(p.z, a.g.lo[2], a.g.inv_w[2], a.g.n[2]);
+    return c;
+}
+
+// Scatter (original index, cell) into the particle's unordered slot.
+__device__ __forceinline__ void coop_scatter(const CoopArgs& a, int64_t tid, int64_t nthreads) {
+    const int64_t n = a.n;
     for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
         uint2 cr[kCoopIlp];
 #pragma unroll
@@ -516,10 +499,13 @@ k_build_coop(CoopArgs a) {
             if (i < n) a.tmp[st[u] + cr[u].y] = make_uint2((uint32_t)i, cr[u].x);
         }
     }
-    coop_barrier(a.bar, a.err, a.limit_ns);
+}
 
-    // P4: stable rank inside the cell (number of members with a smaller
-    // original index), then perm and the sorted positions
+// Stable rank inside the cell (number of members with a smaller original
+// index), then perm and the sorted positions.
+template <int DIM, bool PACKED>
+__device__ __forceinline__ void coop_finalize(const CoopArgs& a, int64_t tid, int64_t nthreads) {
+    const int64_t n = a.n;
     for (int64_t s0 = tid; s0 < n; s0 += nthreads * kCoopIlp) {
         uint2 pc[kCoopIlp];
 #pragma unroll
@@ -548,6 +534,159 @@ k_build_coop(CoopArgs a) {
             a.perm[d] = pc[u].x;
             a.spos[d] = make_float4(q[u].x, q[u].y, DIM == 3 ? q[u].z : 0.0f, 0.0f);
         }
+    }
+}
+
+template <int DIM, bool PACKED>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+k_build_coop(CoopArgs a) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_red[32];
+    const int64_t n = a.n;
+    const int64_t tid = (int64_t)blockIdx.x * kCoopThreads + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * kCoopThreads;
+
+    // P0: zero the counts
+    for (int64_t c = tid; c < a.nc1; c += nthreads) a.cell_start[c] = 0u;
+    coop_barrier(a.bar, a.err, a.limit_ns, (int)blockIdx.x == a.skip_block);
+
+    // P1: cell hash + histogram; the atomic's return is the arrival rank
+    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
+        uint32_t c[kCoopIlp], r[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            c[u] = particle_cell<DIM, PACKED>(a, i < n ? load_pos<DIM, PACKED>(a.pos, i)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            if (i0 + u * nthreads < n) r[u] = atomicAdd(a.cell_start + c[u], 1u);
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            if (i < n) a.cell_rank[i] = make_uint2(c[u], r[u]);
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P2: counts -> offsets (entry n_cells is 0, so the last offset is n)
+    coop_scan_u32(a.cell_start, a.nc1, a, s_warp, s_red);
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P3: scatter; P4: stable finalize
+    coop_scatter(a, tid, nthreads);
+    coop_barrier(a.bar, a.err, a.limit_ns);
+    coop_finalize<DIM, PACKED>(a, tid, nthreads);
+}
+
+template <int DIM, bool PACKED>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+k_build_coop_compact(CoopArgs a) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_red[32];
+    const int64_t n = a.n;
+    const int64_t tid = (int64_t)blockIdx.x * kCoopThreads + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * kCoopThreads;
+
+    // P0: clear the occupancy words and the per-occupied-cell counts (at
+    // most n occupied cells, plus the end entry)
+    for (int64_t w = tid; w < a.n_words; w += nthreads) a.occ[w] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t c = tid; c <= n; c += nthreads) a.cell_start[c] = 0u;
+    coop_barrier(a.bar, a.err, a.limit_ns, (int)blockIdx.x == a.skip_block);
+
+    // P1: cell hash; mark the cell occupied, keep its id
+    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
+        uint32_t c[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            c[u] = particle_cell<DIM, PACKED>(a, i < n ? load_pos<DIM, PACKED>(a.pos, i)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            if (i >= n) continue;
+            atomicOr(reinterpret_cast<unsigned long long*>(a.occ + (c[u] >> 6)), 1ull << (c[u] & 63u));
+            a.cell_rank[i] = make_uint2(c[u], 0u);
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P2: occupied cells before each word (exclusive scan of the words'
+    // popcounts, into occ[w].z)
+    {
+        const int64_t chunk = (a.n_words + gridDim.x - 1) / gridDim.x;
+        const int64_t w0 = (int64_t)blockIdx.x * chunk;
+        const int64_t w1 = w0 + chunk < a.n_words ? w0 + chunk : a.n_words;
+        uint32_t sum = 0;
+        for (int64_t w = w0 + threadIdx.x; w < w1; w += kCoopThreads) {
+            const uint4 q = __ldcg(a.occ + w);
+            sum += (uint32_t)__popc(q.x) + (uint32_t)__popc(q.y);
+        }
+        const uint32_t t = block_sum_u32(sum, s_red);
+        if (threadIdx.x == 0) a.block_sum[blockIdx.x] = t;
+        coop_barrier(a.bar, a.err, a.limit_ns);
+        uint32_t run = earlier_blocks(a.block_sum, s_red);
+        for (int64_t t0 = w0; t0 < w1; t0 += kCoopThreads) {
+            const int64_t w = t0 + threadIdx.x;
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (w < w1) q = __ldcg(a.occ + w);
+            const uint32_t v = (uint32_t)__popc(q.x) + (uint32_t)__popc(q.y);
+            uint32_t total;
+            const uint32_t ex = run + block_excl_scan(v, s_warp, &total);
+            if (w < w1) a.occ[w].z = ex;
+            run += total;
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P3: compact index of each particle's cell; arrival rank in it
+    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
+        uint32_t c[kCoopIlp], k[kCoopIlp], r[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            c[u] = i < n ? ldcg_u2(a.cell_rank + i).x : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const uint4 q = __ldcg(a.occ + (c[u] >> 6));
+            const uint64_t bits = ((uint64_t)q.y << 32) | q.x;
+            k[u] = q.z + (uint32_t)__popcll(bits & ((1ull << (c[u] & 63u)) - 1ull));
+        }
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            if (i0 + u * nthreads < n) r[u] = atomicAdd(a.cell_start + k[u], 1u);
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            if (i < n) a.cell_rank[i] = make_uint2(k[u], r[u]);
+        }
+    }
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P4: counts -> offsets of the occupied cells (entries past the last
+    // occupied cell are 0, so they all become n)
+    coop_scan_u32(a.cell_start, n + 1, a, s_warp, s_red);
+    coop_barrier(a.bar, a.err, a.limit_ns);
+
+    // P5: scatter; P6: stable finalize (over compact indices)
+    coop_scatter(a, tid, nthreads);
+    coop_barrier(a.bar, a.err, a.limit_ns);
+    coop_finalize<DIM, PACKED>(a, tid, nthreads);
+}
+
+// Dense offsets of a compact cell list (inspection and export).
+__global__ void __launch_bounds__(kThreads)
+k_expand_cells(int64_t nc1, const uint4* __restrict__ occ, const uint32_t* __restrict__ cstart,
+               uint32_t* __restrict__ out) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc1;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 q = occ[c >> 6];
+        const uint64_t bits = ((uint64_t)q.y << 32) | q.x;
+        out[c] = cstart[q.z + (uint32_t)__popcll(bits & ((1ull << (c & 63)) - 1ull))];
     }
 }
 
@@ -614,12 +753,20 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
                          uint32_t* err, cudaStream_t st, const BuildOptions& opt) {
     const int64_t n = cl.n;
     const int64_t nc = cl.g.n_cells;
-    // one cooperative launch when the device allows it
-    if (sc.coop && opt.single_launch) {
+    const bool compact = cl.g.compact != 0;
+    // one cooperative launch when the device allows it (always for the
+    // compact table, which has no kernel-sequence form)
+    if (sc.coop && (opt.single_launch || compact)) {
         const void* fn;
-        if (cl.g.dim == 3) fn = packed ? (const void*)k_build_coop<3, true> : (const void*)k_build_coop<3, false>;
-        else fn = packed ? (const void*)k_build_coop<2, true> : (const void*)k_build_coop<2, false>;
-        const int grid = coop_grid(fn, n, nc + 1);
+        if (compact) {
+            if (cl.g.dim == 3) fn = packed ? (const void*)k_build_coop_compact<3, true> : (const void*)k_build_coop_compact<3, false>;
+            else fn = packed ? (const void*)k_build_coop_compact<2, true> : (const void*)k_build_coop_compact<2, false>;
+        } else {
+            if (cl.g.dim == 3) fn = packed ? (const void*)k_build_coop<3, true> : (const void*)k_build_coop<3, false>;
+            else fn = packed ? (const void*)k_build_coop<2, true> : (const void*)k_build_coop<2, false>;
+        }
+        const int64_t n_words = occ_words(nc);
+        const int grid = coop_grid(fn, n, compact ? n_words : nc + 1);
         if (grid >= 1 && grid <= 4096) {
             CoopArgs a;
             a.pos = pos;
@@ -627,6 +774,8 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
             a.g = cl.g;
             a.nc1 = nc + 1;
             a.cell_start = cl.cell_start;
+            a.occ = cl.occ;
+            a.n_words = n_words;
             a.cell_rank = cl.cell_rank;
             a.tmp = reinterpret_cast<uint2*>(cl.tmp);
             a.perm = cl.perm;
@@ -640,10 +789,12 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
             if (e != cudaSuccess) return e;
             void* args[] = {&a};
             e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kCoopThreads), args, 0, st);
-            if (e == cudaSuccess) return cudaSuccess;
+            if (e == cudaSuccess || compact) return e;
             cudaGetLastError();   // not launchable here: fall back to the kernel sequence
         }
+        if (compact) return cudaErrorNotSupported;
     }
+    if (compact) return cudaErrorNotSupported;
     cudaError_t e = cudaMemsetAsync(cl.cell_start, 0, (size_t)(nc + 1) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
@@ -676,6 +827,12 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_expand_cells(const CellList& cl, uint32_t* out, cudaStream_t st) {
+    const int64_t nc1 = cl.g.n_cells + 1;
+    k_expand_cells<<<ew_grid(nc1), kThreads, 0, st>>>(nc1, cl.occ, cl.cell_start, out);
+    return cudaGetLastError();
 }
 
 // A per-particle scalar in sorted order: out[s] = v[perm[s]].

@@ -32,6 +32,7 @@ struct Geom {
     int general;         // 1 if a periodic axis has fewer than 5 cells
     int kx;              // x cells per cut-off width: the stencil spans cx - kx .. cx + kx
     int ky, kz;          // the same for y and z (stencil rows: (2 ky + 1) (2 kz + 1))
+    int compact;         // 1: offsets of occupied cells only, found through CellList::occ
     int64_t n_cells;
 };
 
@@ -55,9 +56,17 @@ struct CellList {
     uint32_t* perm = nullptr;         // perm[s] = original index
     uint2* cell_rank = nullptr;       // per original particle: (cell, atomic arrival rank)
     uint32_t* tmp = nullptr;          // unordered slot -> original index
-    uint32_t* cell_start = nullptr;   // [n_cells + 1]
+    uint32_t* cell_start = nullptr;   // dense: [n_cells + 1]; compact: [n + 1], per occupied cell
     size_t cap_n = 0, cap_cells = 0;
+    // compact table: per 64 cells, the occupancy bits (x: cells 0-31, y:
+    // 32-63) and the number of occupied cells before them (z)
+    uint4* occ = nullptr;
+    size_t cap_occ = 0;
 };
+
+// Words of the occupancy table of a compact cell list (cells 0 .. n_cells,
+// the last one past the end).
+inline int64_t occ_words(int64_t n_cells) { return (n_cells + 1 + 63) / 64; }
 
 struct Scratch {
     float2* sv = nullptr;             // sorted per-particle values: (m, P/rho^2) for the SPH
@@ -91,6 +100,9 @@ AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, 
                                    uint32_t* err, cudaStream_t st, const BuildOptions& opt);
 // words of Scratch::coop (allocated once per context)
 AB_HIDDEN size_t coop_scratch_words();
+// The dense offsets of a compact cell list: out[c] = first slot of cell c,
+// c = 0 .. n_cells (device uint32[n_cells + 1]).
+AB_HIDDEN cudaError_t launch_expand_cells(const CellList& cl, uint32_t* out, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_w_pos(CellList& cl, const float* w, cudaStream_t st);
 AB_HIDDEN cudaError_t launch_gather_scalar(const CellList& cl, const float* v, float* out,
                                            cudaStream_t st);

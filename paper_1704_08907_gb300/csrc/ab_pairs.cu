@@ -34,7 +34,8 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 struct PairParams {
     const float4* __restrict__ spos;
-    const uint32_t* __restrict__ cell_start;
+    const uint32_t* __restrict__ cell_start;   // dense: per cell; compact: per occupied cell
+    const uint4* __restrict__ occ;             // compact: occupancy words (see cell_bound)
     const uint32_t* __restrict__ perm;
     const float2* __restrict__ sv;
     int64_t n;
@@ -124,13 +125,33 @@ __device__ __forceinline__ float value_sep(float xi, float xj, bool periodic, fl
     return s;
 }
 
+// Kernel modes: the fast path over a dense cell table, the general path
+// (canonical wrap per candidate, dense table), and the fast path over the
+// compacted table of occupied cells.
+constexpr int kModeFast = 0, kModeGeneral = 1, kModeCompact = 2;
+
+// First sorted slot of cell c (c = n_cells gives n).  Dense table: one load.
+// Compacted table: occ[c / 64] packs the occupancy bits of cells 64w ..
+// 64w + 63 (x, y) and the number of occupied cells before them (z); the
+// occupied cells before c index the compact offsets (an empty cell starts
+// where the next occupied one does).
+template <int MODE>
+__device__ __forceinline__ uint32_t cell_bound(const PairParams& P, int64_t c) {
+    if (MODE != kModeCompact) return __ldg(P.cell_start + c);
+    const uint4 q = __ldg(P.occ + (c >> 6));
+    const uint64_t bits = ((uint64_t)q.y << 32) | q.x;
+    const uint32_t rank = q.z + (uint32_t)__popcll(bits & ((1ull << (c & 63)) - 1ull));
+    return __ldg(P.cell_start + rank);
+}
+
 // Walk the stencil of the particle at pi: seg(a, b, sx, sy, sz) is called for
 // each contiguous range [a, b) of sorted particles with its fast-path shift.
 // Rows along x are contiguous in sorted order; a row that wraps through the
 // periodic x face splits into two segments.
-template <int DIM, bool GENERAL, class S>
+template <int DIM, int MODE, class S>
 __device__ __forceinline__ void for_each_segment(const PairParams& P, const float4& pi,
                                                  S&& seg) {
+    constexpr bool GENERAL = MODE == kModeGeneral;
     const Geom& g = P.g;
     const int cx = cell_coord(pi.x, g.lo[0], g.inv_w[0], g.n[0]);
     const int cy = cell_coord(pi.y, g.lo[1], g.inv_w[1], g.n[1]);
@@ -168,9 +189,9 @@ __device__ __forceinline__ void for_each_segment(const PairParams& P, const floa
             if (!stencil_coord(g, 1, cy, oy, y, sy)) continue;
             if (GENERAL) sy = sz = 0.0f;
             const int64_t row = ((int64_t)z * g.n[1] + y) * nx;
-            seg(__ldg(P.cell_start + row + xa0), __ldg(P.cell_start + row + xb0 + 1), xs0, sy, sz);
+            seg(cell_bound<MODE>(P, row + xa0), cell_bound<MODE>(P, row + xb0 + 1), xs0, sy, sz);
             if (xb1 >= xa1)
-                seg(__ldg(P.cell_start + row + xa1), __ldg(P.cell_start + row + xb1 + 1), xs1, sy, sz);
+                seg(cell_bound<MODE>(P, row + xa1), cell_bound<MODE>(P, row + xb1 + 1), xs1, sy, sz);
         }
     }
 }
@@ -240,12 +261,13 @@ __device__ __forceinline__ float pred_d2(const Geom& g, const float4& pi, const 
 // kernel.  UNROLL is the unroll factor of the candidate loop, measured per
 // kernel: 2 where the body is short or rarely taken (forwards, COUNT, the
 // fused LJ kernel), 4 for the adjoints and the EXPF / SOFT forces.
-template <int DIM, bool GENERAL, int UNROLL = 4, class F>
+template <int DIM, int MODE, int UNROLL = 4, class F>
 __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
                                             const float4& pi, F&& f) {
+    constexpr bool GENERAL = MODE == kModeGeneral;
     const Geom& g = P.g;
     const float r2 = g.r2;
-    for_each_segment<DIM, GENERAL>(P, pi, [&](uint32_t a0, uint32_t b0, float sx, float sy,
+    for_each_segment<DIM, MODE>(P, pi, [&](uint32_t a0, uint32_t b0, float sx, float sy,
                                               float sz) {
       // the segment holding the particle itself is walked as [a0, s), (s, b0)
       uint32_t a = a0, b = (a0 <= s && s < b0) ? s : b0;
@@ -298,14 +320,14 @@ __device__ __forceinline__ void block_partial(double v, double* partial) {
 // Forward for the cheap operators (COUNT, GAUSS, SPH density): direct visit.
 // The weight w_j (GAUSS) or mass m_j (SPH) comes in the pad component of the
 // sorted position, loaded with the candidate.
-template <int DIM, bool GENERAL, int OP>
+template <int DIM, int MODE, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
     float a0 = 0.0f;
-    visit_pairs<DIM, GENERAL, 2>(P, s, pi,
+    visit_pairs<DIM, MODE, 2>(P, s, pi,
         [&](uint32_t, const float4& pj, float, float, float, float d2) {
             if (OP == AB_OP_COUNT) {
                 a0 += 1.0f;
@@ -323,7 +345,7 @@ k_pair_fwd(PairParams P, PairOut o) {
 }
 
 // Forward for LJ / EXPF / SOFT: direct visit.
-template <int DIM, bool GENERAL, int OP>
+template <int DIM, int MODE, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd_q(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
@@ -331,7 +353,7 @@ k_pair_fwd_q(PairParams P, PairOut o) {
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
     const float ai = (OP == AB_OP_SPH_FORCE && live) ? __ldg(&P.sv[s].y) : 0.0f;
-    if (live) visit_pairs<DIM, GENERAL, (OP == AB_OP_EXPF || OP == AB_OP_SOFT) ? 4 : 2>(P, s, pi,
+    if (live) visit_pairs<DIM, MODE, (OP == AB_OP_EXPF || OP == AB_OP_SOFT) ? 4 : 2>(P, s, pi,
         [&](uint32_t j, const float4&, float dx, float dy, float dz, float d2) {
             if (OP == AB_OP_SPH_FORCE) {
                 // m_j (A_i + A_j) W'(d)/d dx, W'(d)/d = wend_grad t^3
@@ -386,7 +408,7 @@ k_pair_fwd_q(PairParams P, PairOut o) {
 // the forward kernel's expression, accumulated in the same visit order, so
 // both outputs equal the separate kernels' bit for bit.  With VALUE the
 // partials carry the LJ energy (GAUSS: still ds).
-template <int DIM, bool GENERAL, int OP, bool VALUE>
+template <int DIM, int MODE, int OP, bool VALUE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_bwd(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
@@ -397,7 +419,7 @@ k_pair_bwd(PairParams P, PairOut o) {
     const float* __restrict__ wv = reinterpret_cast<const float*>(P.sv);
     const float wi = (live && OP == AB_OP_GAUSS) ? __ldg(wv + s) : 0.0f;
     float gx = 0.0f, gy = 0.0f, gz = 0.0f, dw = 0.0f, ds = 0.0f, y = 0.0f;
-    if (live) visit_pairs<DIM, GENERAL>(P, s, pi,
+    if (live) visit_pairs<DIM, MODE>(P, s, pi,
         [&](uint32_t j, const float4& pj, float dx, float dy, float dz, float d2) {
             if (OP == AB_OP_GAUSS) {
                 const float wj = __ldg(wv + j);
@@ -447,14 +469,14 @@ k_pair_bwd(PairParams P, PairOut o) {
 // predicate and the powers of sig/d.  Bit for bit the results of k_pair_fwd_q
 // (LJ) and of k_pair_bwd (LJ) with g = 1: the same visit order, the same
 // expressions, and (g_i + g_j) = 2 exactly.
-template <int DIM, bool GENERAL>
+template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_lj_eg(PairParams P, PairOut o) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
     float e = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
-    if (live) visit_pairs<DIM, GENERAL, 2>(P, s, pi,
+    if (live) visit_pairs<DIM, MODE, 2>(P, s, pi,
         [&](uint32_t, const float4&, float dx, float dy, float dz, float d2) {
             const float inv = rcp_approx(d2);
             const float sr2 = P.sig2 * inv;
@@ -484,26 +506,26 @@ k_pair_lj_eg(PairParams P, PairOut o) {
     if (o.partial) block_partial<kPairThreads>(live ? (double)e : 0.0, o.partial);
 }
 
-template <int DIM, bool GENERAL>
+template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
     uint32_t c = 0;
-    visit_pairs<DIM, GENERAL, 2>(P, s, pi,
+    visit_pairs<DIM, MODE, 2>(P, s, pi,
         [&](uint32_t, const float4&, float, float, float, float) { ++c; });
     counts[__ldg(P.perm + s)] = c;
 }
 
-template <int DIM, bool GENERAL>
+template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_emit(PairParams P, const int64_t* __restrict__ offsets, int32_t* __restrict__ idx) {
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
     int64_t at = offsets[__ldg(P.perm + s)];
-    visit_pairs<DIM, GENERAL, 2>(P, s, pi,
+    visit_pairs<DIM, MODE, 2>(P, s, pi,
         [&](uint32_t j, const float4&, float, float, float, float) {
             idx[at++] = (int32_t)__ldg(P.perm + j);
         });
@@ -513,6 +535,7 @@ PairParams make_params(const CellList& cl, const ab_op_params& prm, const float2
     PairParams P;
     P.spos = cl.spos;
     P.cell_start = cl.cell_start;
+    P.occ = cl.occ;
     P.perm = cl.perm;
     P.sv = sv;
     P.n = cl.n;
@@ -543,11 +566,13 @@ int pair_grid(int64_t n) { return (int)((n + kPairThreads - 1) / kPairThreads); 
     do {                                                                              \
         const int grid = (int)((cl.n + THREADS - 1) / THREADS);                       \
         if (cl.g.dim == 3) {                                                          \
-            if (cl.g.general) KERNEL<3, true OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
-            else KERNEL<3, false OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);       \
+            if (cl.g.general) KERNEL<3, kModeGeneral OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
+            else if (cl.g.compact) KERNEL<3, kModeCompact OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
+            else KERNEL<3, kModeFast OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);   \
         } else {                                                                      \
-            if (cl.g.general) KERNEL<2, true OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
-            else KERNEL<2, false OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);       \
+            if (cl.g.general) KERNEL<2, kModeGeneral OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
+            else if (cl.g.compact) KERNEL<2, kModeCompact OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
+            else KERNEL<2, kModeFast OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);   \
         }                                                                             \
     } while (0)
 

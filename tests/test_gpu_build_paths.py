@@ -96,3 +96,44 @@ def test_single_launch_barrier_timeout_reports_and_recovers(ab, ctx):
     off, _ = oracle.neighbours_brute(oracle_box(w), w.pos)
     assert np.array_equal(c, np.diff(off).astype(np.float32))
     ab.ab_sync(ctx)
+
+
+@pytest.mark.parametrize("case", ["c2", "clustered", "2d_wall", "one_cell", "n1", "n2"])
+def test_compact_table_equals_dense_table(ab, ctx, case):
+    """The table of occupied cells orders particles and finds stencil rows
+    exactly as the dense table: same permutation, same offsets of every
+    cell, same pair sums bit for bit."""
+    dim, periodic, r, pos = _case(case)
+    ab.ab_testing_build_path(ctx, True)
+    out = {}
+    for mode in (1, 2):
+        ab.ab_testing_cell_table(ctx, mode)
+        dom = ab.Domain(dim, periodic, r)
+        ab.ab_build(ctx, dom, dev(pos))
+        perm, start = ab.ab_cell_export(ctx)
+        cnt = ab.ab_pair_sum(ctx, "count", ab.OpParams())
+        wt = dev(synth.weights(len(pos), 3, "normal"))
+        y = ab.ab_pair_sum(ctx, "gauss", ab.OpParams(s=1.0 / (r / 3) ** 2), w=wt)
+        E, G, e = ab.ab_pair_energy_grad(ctx, "lj", ab.OpParams(eps=1.0, sigma=r / 3))
+        ab.ab_sync(ctx)
+        out[mode] = [host(t) for t in (perm, start, cnt, y, E, G)] + [float(e)]
+    ab.ab_testing_cell_table(ctx, 0)
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(np.asarray(a), np.asarray(b), equal_nan=True)
+
+
+def test_compact_table_is_chosen_for_clustered_points(ab, ctx):
+    """Automatic choice: the clustered workload's lattice has more than 4
+    cells a particle, so the compact table is used; its neighbour counts
+    match the oracle on sampled rows."""
+    w = synth.c3(n=1 << 18, n_blobs=16)
+    ab.ab_testing_cell_table(ctx, 0)
+    ab.ab_testing_build_path(ctx, True)
+    ab.ab_build(ctx, ab.Domain(3, w.periodic, w.radius), dev(w.pos))
+    _, ncells, _ = ab.ab_cell_shape(ctx, with_reach=True)
+    assert ncells > 4 * w.n
+    c = host(ab.ab_pair_sum(ctx, "count", ab.OpParams()))
+    q = synth.query_sample(w.n, 2048, 7)
+    off, _ = oracle.CellList(oracle_box(w), w.pos).neighbours(q)
+    assert np.array_equal(c[q], np.diff(off).astype(np.float32))
+    ab.ab_sync(ctx)
