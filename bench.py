@@ -54,8 +54,8 @@ OPS_PER_PAIR_LJ_EG = 12
 # DRAM traffic of one k_pair_lj_eg<3,false> launch on this workload, from an
 # ncu --set full capture (dram__bytes_read.sum + dram__bytes_write.sum), valid
 # only for the kernel source it was taken on (None until captured).
-TRAFFIC_EG_BYTES = 35.44e6   # 29.21 MB read + 6.23 MB written
-TRAFFIC_SOURCE_SHA = "3bd5c6d60cbc41b7"
+TRAFFIC_EG_BYTES = 35.43e6   # 29.21 MB read + 6.22 MB written
+TRAFFIC_SOURCE_SHA = "8969d64f49db79a0"
 
 
 def alu_peak(pk):
@@ -394,7 +394,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": pos_h.numel() * 4,
                 "d2h_bytes_per_step": F_h.numel() * 4 + 8},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 3 * args.steps,   # build (one cooperative launch), fused walk, energy reduction
         "wall_s": wall,
     }
     if clk:
@@ -527,8 +527,9 @@ def oracle_sample_c3(w, nq, seed=23):
 # DRAM traffic of one k_pair_bwd<3,false,GAUSS> launch on the clustered
 # workload (ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the
 # kernel source whose hash is given (None until captured on that source).
-TRAFFIC_C3_BWD_BYTES = None
-TRAFFIC_C3_SOURCE_SHA = None
+TRAFFIC_C3_BWD_BYTES = 944.05e6    # 551.41 MB read + 392.64 MB written (adjoint kernel)
+TRAFFIC_C3_VG_BYTES = 1131.02e6    # 613.29 MB read + 517.74 MB written (value and gradient)
+TRAFFIC_C3_SOURCE_SHA = "8969d64f49db79a0"
 
 
 def also_c3(reps=5, oracle_fraction=64):
@@ -618,7 +619,7 @@ def also_c3(reps=5, oracle_fraction=64):
            "pairs_per_s": pairs / (ms * 1e-3), "inputs_larger_than_l2": True,
            "phases_ms": {"build": ph[0], "fwd": ph[1], "bwd": ph[2]},
            "cells": list(ncell), "n_cells": ncells, "cell_split": list(reach),
-           "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,false,GAUSS> (adjoint: x, w, s)",
+           "roofline": {"bound": "alu", "kernel": "k_pair_bwd<3,compact,GAUSS> (adjoint: x, w, s)",
                         "achieved": bwd_ops / (ph[2] * 1e-3) / 1e12, "peak": alu, "unit": "Top/s",
                         "frac": bwd_ops / (ph[2] * 1e-3) / 1e12 / alu,
                         "traffic": TRAFFIC_C3_BWD_BYTES if same else None,
@@ -633,7 +634,8 @@ def also_c3(reps=5, oracle_fraction=64):
                "phases_ms": {"build": vg_ph[0], "value_and_grad": vg_ph[1]},
                "alu_frac": (cands * OPS_PER_CANDIDATE + pairs * (OPS_PER_PAIR_GAUSS_FWD +
                                                                  OPS_PER_PAIR_GAUSS_BWD))
-                           / (vg_ph[1] * 1e-3) / 1e12 / alu},
+                           / (vg_ph[1] * 1e-3) / 1e12 / alu,
+               "traffic": TRAFFIC_C3_VG_BYTES if same else None},
            "build_hbm_frac": bbytes / (ph[0] * 1e-3) / 1e9 / pk["hbm_gbs"],
            "build_bytes_algorithmic": bbytes}
     nq = w.n // oracle_fraction
