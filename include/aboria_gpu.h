@@ -150,9 +150,10 @@ ab_status ab_sync(ab_ctx* ctx);
  * empty), the library keeps offsets of the occupied cells only, with a
  * bitmap of occupied cells to find them (about 0.25 bytes a cell plus 4 a
  * particle instead of 4 bytes a cell); the order and every result are the
- * same bit for bit.  The build runs as one cooperative launch whose phases
- * are separated by grid barriers with bounded waits (a wait that gives up is
- * reported by ab_sync as AB_ERR_TIMEOUT).
+ * same bit for bit.  Up to 2^21 particles, and for every compact table, the
+ * build runs as one cooperative launch whose phases are separated by grid
+ * barriers with bounded waits (a wait that gives up is reported by ab_sync
+ * as AB_ERR_TIMEOUT); larger dense builds run as a sequence of kernels.
  *   dom:  host pointer to the domain (copied).
  *   n:    number of particles, 0 <= n < 2^31.
  *   pos4: float32[n][4] device positions (16-byte aligned).

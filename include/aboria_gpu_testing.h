@@ -37,9 +37,10 @@ ab_status ab_testing_cell_table(ab_ctx* ctx, int32_t mode);
 
 /* Select how the following ab_build calls run: single_launch = 1 (the
  * default) builds the cell list in one cooperative launch whose phases are
- * separated by bounded grid-wide barriers; 0 runs the same counting sort as
- * a sequence of kernels (a compact table is always built in one launch).
- * Both give the same cell list bit for bit.
+ * separated by bounded grid-wide barriers (above 2^21 particles with a dense
+ * table the kernel sequence is used, being faster there); 0 always runs the
+ * same counting sort as a sequence of kernels (a compact table is always
+ * built in one launch).  Both give the same cell list bit for bit.
  * Errors: AB_ERR_INVALID_ARG. */
 ab_status ab_testing_build_path(ab_ctx* ctx, int32_t single_launch);
 
