@@ -137,3 +137,33 @@ def test_scan_wait_times_out_without_hanging(ab, ctx):
     box = oracle_box(w)
     off, _ = oracle.neighbours_brute(box, w.pos)
     assert np.array_equal(c, np.diff(off).astype(np.float32))
+
+
+def test_bd_time_loop_statistics(ab, ctx):
+    """1000 steps of the Brownian loop (rebuild + soft force + step, every
+    step) on 4M points in the dilute limit (r = 2e-5, so almost no pair
+    interacts): per-axis mean squared displacement 2 D t within 1%, every x
+    in [0, 1) and every y in [0, 1] (periodic x, reflecting y)."""
+    w = synth.c5()
+    p = w.params
+    r = 2e-5
+    dom = ab.Domain(2, w.periodic, r)
+    prm = ab.OpParams(k=p["k"])
+    pos0 = w.pos.copy()
+    pos0[:, 1] = np.float32(0.25) + np.float32(0.5) * pos0[:, 1]   # away from the walls
+    pos = dev(pos0)
+    F = torch.empty_like(pos)
+    steps = 1000
+    for t in range(steps):
+        ab.ab_build(ctx, dom, pos)
+        ab.ab_pair_sum(ctx, "soft", prm, out=F)
+        ab.ab_bd_step(ctx, dom, pos, F, p["dt"], p["D"], p["seed"], t)
+    ab.ab_sync(ctx)
+    out = host(pos)
+    assert np.all(out[:, 0] >= 0) and np.all(out[:, 0] < 1)
+    assert np.all(out[:, 1] >= 0) and np.all(out[:, 1] <= 1)
+    d = out[:, :2].astype(np.float64) - pos0[:, :2].astype(np.float64)
+    d[:, 0] -= np.round(d[:, 0])                       # minimum image along periodic x
+    msd = (d * d).mean(0)
+    expect = 2 * p["D"] * p["dt"] * steps
+    assert np.all(np.abs(msd / expect - 1) < 0.01), msd / expect
