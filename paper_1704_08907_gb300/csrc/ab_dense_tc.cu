@@ -11,13 +11,13 @@
 //                       per element), p = ex2 of it, p split into
 //                       bf16 p_hi + p_lo, both written to TMEM with
 //                       tcgen05.st (the A operand of the next MMA);
-//   warp 16 (one thread) tcgen05.mma kind::f16 / kind::tf32, A = P from TMEM,
+//   warp 16 (one elected lane) tcgen05.mma kind::f16 / kind::tf32, A = P from TMEM,
 //                       B = W tile from shared memory, FP32 accumulator in
 //                       TMEM: split paths D[128 x 128] += (P_hi + P_lo)
 //                       [W_hi | W_lo] (two N = 128 MMAs per K step; the
 //                       result is D[:, :64] + D[:, 64:]); plain paths
 //                       D[128 x 64] += P_hi W_hi;
-//   warp 17 (one thread) cp.async.bulk of the next W tiles into a 3-stage ring.
+//   warp 17 (one elected lane) cp.async.bulk of the next W tiles into a 3-stage ring.
 // W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
 // tile by tile in exactly the shared-memory image the MMA reads (K-major,
 // 128-byte swizzle), so each tile arrives by one contiguous bulk copy.
@@ -115,6 +115,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+// One lane of a converged warp (elect.sync).  The MMA and producer roles run
+// their loops on the whole warp and issue tcgen05.mma, tcgen05.commit and the
+// bulk copies from the elected lane: issued from inside a one-lane branch
+// instead, each of these warp-uniform instructions is wrapped by the compiler
+// in a loop over the active lanes (about ten extra instructions per MMA on the
+// scheduler that also runs epilogue warps).
+__device__ __forceinline__ bool elect_one_sync() {
+    uint32_t pred = 0;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "elect.sync _|P, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(pred));
+    return pred != 0;
 }
 // Bounded wait on a phase parity.  Returns false if this CTA aborted (here or
 // in another role); raises the abort flag and the device error on timeout.
@@ -495,26 +510,32 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
 
     if (warp == kEpiWarps + 1) {
         // ---------------- producer: W tiles into the ring ----------------
-        if (lane == 0) {
-            int64_t issued = 0;
-            for (int64_t t = 0; t < tiles; ++t) {
-                const int s = (int)(t % kFwdStages);
-                const uint32_t use = (uint32_t)(t / kFwdStages);
-                if (t >= kFwdStages && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, abort_flag, err))
-                    break;
-                const int64_t gt = t_begin + t;
+        int64_t issued = 0;
+        int s = 0;
+        uint32_t ph = 0;   // (t / kFwdStages) & 1
+        for (int64_t t = 0; t < tiles; ++t) {
+            if (t >= kFwdStages) {
+                const bool ok = mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, err);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            const int64_t gt = t_begin + t;
+            if (elect_one_sync()) {
                 mbar_arrive_expect_tx(bar_full + 8 * s, kStageBytes);
                 bulk_copy(sbase + SmemLayout::w + s * kStageBytes, wimg + gt * (int64_t)kImgBytes,
                           kImgBytes, bar_full + 8 * s);
                 bulk_copy(sbase + SmemLayout::w + s * kStageBytes + kImgBytes, Yhat + gt * kTN, kYBytes,
                           bar_full + 8 * s);
-                issued = t + 1;
             }
-            // copies still in flight must land before the CTA may exit
+            __syncwarp();
+            issued = t + 1;
+            if (++s == kFwdStages) { s = 0; ph ^= 1u; }
+        }
+        // copies still in flight must land before the CTA may exit
+        if (lane == 0) {
             for (int64_t t = issued > kFwdStages ? issued - kFwdStages : 0; t < issued; ++t) {
-                const int s = (int)(t % kFwdStages);
+                const int q = (int)(t % kFwdStages);
                 const long long t0 = gtimer();
-                while (!mbar_try_wait(bar_full + 8 * s, (uint32_t)(t / kFwdStages) & 1)) {
+                while (!mbar_try_wait(bar_full + 8 * q, (uint32_t)(t / kFwdStages) & 1)) {
                     if (gtimer() - t0 > kWaitLimitNs) {
                         atomicOr(err, DEVERR_TC_TIMEOUT);
                         break;
@@ -523,23 +544,26 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             }
         }
     } else if (warp == kEpiWarps) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            for (int64_t t = 0; t < tiles; ++t) {
-                const int s = (int)(t % kFwdStages);
-                const int b = (int)(t % kPBufs);
-                if (!mbar_wait(bar_full + 8 * s, (uint32_t)(t / kFwdStages) & 1, abort_flag, err)) break;
-                if (!mbar_wait(bar_pfull + 8 * b, (uint32_t)(t / kPBufs) & 1, abort_flag, err)) break;
-                tc_fence_after();
-                const uint32_t a_hi = tmem + kColP + 128 * b;
-                const uint32_t a_lo = a_hi + 64;
-                const uint32_t wb = sbase + SmemLayout::w + s * kStageBytes;
+        // ---------------- MMA issuer: the warp waits, one lane issues ----------------
+        int s = 0, b = 0;
+        uint32_t sph = 0, bph = 0;   // (t / kFwdStages) & 1, (t / kPBufs) & 1
+        for (int64_t t = 0; t < tiles; ++t) {
+            bool ok = mbar_wait(bar_full + 8 * s, sph, abort_flag, err);
+            ok = ok && mbar_wait(bar_pfull + 8 * b, bph, abort_flag, err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const uint32_t a_hi = tmem + kColP + 128 * b;
+            const uint32_t a_lo = a_hi + 64;
+            // descriptor of the stage; K step ks starts (ks / 4) 16 KB + (ks % 4)
+            // 32 bytes further (the address field counts 16-byte units)
+            const uint64_t d0 = sw128_desc(sbase + SmemLayout::w + s * kStageBytes);
+            if (elect_one_sync()) {
                 // 8 K steps of 32 bytes (16 bf16 or 8 tf32 points = 8 TMEM columns);
                 // split: D[:, 0:128] += (P_hi + P_lo) [W_hi | W_lo] as two N = 128
                 // MMAs (the extra P_lo W_lo term only adds accuracy)
 #pragma unroll
                 for (int ks = 0; ks < 8; ++ks) {
-                    const uint64_t bdesc = sw128_desc(wb + (ks / 4) * 16384 + (ks % 4) * 32);
+                    const uint64_t bdesc = d0 + (uint64_t)(((ks / 4) * 16384 + (ks % 4) * 32) >> 4);
                     const uint32_t acol = ks * 8;
                     const uint32_t acc0 = (t > 0 || ks > 0) ? 1u : 0u;
                     if (TF32) {
@@ -561,10 +585,14 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 tc_commit(bar_empty + 8 * s);
                 tc_commit(bar_pempty + 8 * b);
             }
-            // always signal the epilogue; after an abort it only waits for the
-            // MMAs already issued before freeing TMEM
-            tc_commit(bar_acc);
+            __syncwarp();
+            if (++s == kFwdStages) { s = 0; sph ^= 1u; }
+            if (++b == kPBufs) { b = 0; bph ^= 1u; }
         }
+        // always signal the epilogue; after an abort it only waits for the
+        // MMAs already issued before freeing TMEM
+        if (elect_one_sync()) tc_commit(bar_acc);
+        __syncwarp();
     } else {
         // ---------------- epilogue warps: row i, one column half ----------------
         const int quad = warp & 3, part = warp >> 2;   // lane quadrant, column slice
@@ -922,26 +950,37 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
     const int64_t row0 = (int64_t)blockIdx.x * kTM;
 
     if (warp == kEpiWarps + 1) {
-        if (lane == 0) {
+        // producer: the warp waits, one elected lane copies
+        if (elect_one_sync()) {
             mbar_arrive_expect_tx(bar_afull, kGImg);
             bulk_copy(sbase + GradSmem::a, gimg + blockIdx.x * (int64_t)kGImg, kGImg, bar_afull);
-            int64_t issued = 0;
-            for (int64_t t = 0; t < tiles; ++t) {
-                const int q = (int)(t % kStages);
-                const uint32_t use = (uint32_t)(t / kStages);
-                if (t >= kStages && !mbar_wait(bar_empty + 8 * q, (use - 1) & 1, abort_flag, err)) break;
-                const int64_t gt = t_begin + t;
+        }
+        __syncwarp();
+        int64_t issued = 0;
+        int q = 0;
+        uint32_t ph = 0;   // (t / kStages) & 1
+        for (int64_t t = 0; t < tiles; ++t) {
+            if (t >= kStages) {
+                const bool ok = mbar_wait(bar_empty + 8 * q, ph ^ 1u, abort_flag, err);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            const int64_t gt = t_begin + t;
+            if (elect_one_sync()) {
                 mbar_arrive_expect_tx(bar_full + 8 * q, kGStage);
                 bulk_copy(sbase + GradSmem::ring + q * kGStage, wimg + gt * (int64_t)kGImg, kGImg,
                           bar_full + 8 * q);
                 bulk_copy(sbase + GradSmem::ring + q * kGStage + kGImg, Yt + gt * 128, 128 * 16,
                           bar_full + 8 * q);
-                issued = t + 1;
             }
+            __syncwarp();
+            issued = t + 1;
+            if (++q == kStages) { q = 0; ph ^= 1u; }
+        }
+        if (lane == 0) {
             for (int64_t t = issued > kStages ? issued - kStages : 0; t < issued; ++t) {
-                const int q = (int)(t % kStages);
+                const int qq = (int)(t % kStages);
                 const long long t0 = gtimer();
-                while (!mbar_try_wait(bar_full + 8 * q, (uint32_t)(t / kStages) & 1)) {
+                while (!mbar_try_wait(bar_full + 8 * qq, (uint32_t)(t / kStages) & 1)) {
                     if (gtimer() - t0 > kWaitLimitNs) {
                         atomicOr(err, DEVERR_TC_TIMEOUT);
                         break;
@@ -957,25 +996,29 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             }
         }
     } else if (warp == kEpiWarps) {
-        if (lane == 0) {
-            bool ok = mbar_wait(bar_afull, 0, abort_flag, err);
-            for (int64_t t = 0; ok && t < tiles; ++t) {
-                const int q = (int)(t % kStages);
-                const int b = (int)(t & 1);
-                if (!mbar_wait(bar_full + 8 * q, (uint32_t)(t / kStages) & 1, abort_flag, err)) break;
-                if (t >= 2 && !mbar_wait(bar_sempty + 8 * b, (uint32_t)((t - 2) >> 1) & 1, abort_flag, err))
-                    break;
-                tc_fence_after();
-                const uint32_t ga = sbase + GradSmem::a;
-                const uint32_t wb = sbase + GradSmem::ring + q * kGStage;
-                const uint32_t dcol = tmem + 128 * b;
+        // MMA issuer: the warp waits, one elected lane issues
+        const bool aok = __all_sync(0xffffffffu, mbar_wait(bar_afull, 0, abort_flag, err));
+        int q = 0;
+        uint32_t qph = 0;   // (t / kStages) & 1
+        // descriptors of the G image (hi at 0, lo 16 KB further); K step ks
+        // starts ks 32 bytes further (the address field counts 16-byte units)
+        const uint64_t ga0 = sw128_desc(sbase + GradSmem::a);
+        for (int64_t t = 0; aok && t < tiles; ++t) {
+            const int b = (int)(t & 1);
+            bool ok = mbar_wait(bar_full + 8 * q, qph, abort_flag, err);
+            if (t >= 2) ok = ok && mbar_wait(bar_sempty + 8 * b, (uint32_t)((t - 2) >> 1) & 1, abort_flag, err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const uint64_t wb0 = sw128_desc(sbase + GradSmem::ring + q * kGStage);
+            const uint32_t dcol = tmem + 128 * b;
+            if (elect_one_sync()) {
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t ahi = sw128_desc(ga + ks * 32), bhi = sw128_desc(wb + ks * 32);
+                    const uint64_t ahi = ga0 + (uint64_t)(ks * 2), bhi = wb0 + (uint64_t)(ks * 2);
                     mma_ss(dcol, ahi, bhi, kIdescBf16N128, ks > 0 ? 1u : 0u);
                     if (SPLIT) {
-                        const uint64_t alo = sw128_desc(ga + 16384 + ks * 32);
-                        const uint64_t blo = sw128_desc(wb + 16384 + ks * 32);
+                        const uint64_t alo = ahi + (uint64_t)(16384 >> 4);
+                        const uint64_t blo = bhi + (uint64_t)(16384 >> 4);
                         mma_ss(dcol, ahi, blo, kIdescBf16N128, 1u);
                         mma_ss(dcol, alo, bhi, kIdescBf16N128, 1u);
                     }
@@ -983,10 +1026,13 @@ k_dense_tc_gradx(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 tc_commit(bar_sfull + 8 * b);
                 tc_commit(bar_empty + 8 * q);
             }
-            // completes once every MMA issued above has finished (also after
-            // an abort); waited for before TMEM is released
-            tc_commit(bar_done);
+            __syncwarp();
+            if (++q == kStages) { q = 0; qph ^= 1u; }
         }
+        // completes once every MMA issued above has finished (also after
+        // an abort); waited for before TMEM is released
+        if (elect_one_sync()) tc_commit(bar_done);
+        __syncwarp();
     } else {
         // Warp w serves TMEM lane quadrant w % 4, lane half (w / 4) % 2 and
         // columns 64 (w / 8) .. +63 of each S tile.  Thread (g4, c4) =
