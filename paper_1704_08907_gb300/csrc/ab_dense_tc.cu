@@ -13,10 +13,10 @@
 //                       tcgen05.st (the A operand of the next MMA);
 //   warp 16 (one elected lane) tcgen05.mma kind::f16 / kind::tf32, A = P from TMEM,
 //                       B = W tile from shared memory, FP32 accumulator in
-//                       TMEM: split paths D[128 x 128] += (P_hi + P_lo)
-//                       [W_hi | W_lo] (two N = 128 MMAs per K step; the
-//                       result is D[:, :64] + D[:, 64:]); plain paths
-//                       D[128 x 64] += P_hi W_hi;
+//                       TMEM: split paths D[128 x 128] += P_hi [W_hi | W_lo]
+//                       (N = 128) and D[:, :64] += P_lo W_hi (N = 64) per K
+//                       step; the result is D[:, :64] + D[:, 64:]; plain
+//                       paths D[128 x 64] += P_hi W_hi;
 //   warp 17 (one elected lane) cp.async.bulk of the next W tiles into a 3-stage ring.
 // W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
 // tile by tile in exactly the shared-memory image the MMA reads (K-major,
@@ -31,6 +31,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "ab_internal.cuh"
 
@@ -77,7 +79,8 @@ struct SmemLayout {
     static constexpr int accfull = pempty + 8 * kPBufs;
     static constexpr int tmem_slot = accfull + 8;
     static constexpr int abort_flag = tmem_slot + 4;
-    static constexpr int bytes = abort_flag + 4;
+    static constexpr int fold_max = abort_flag + 4;   // bits of max over the rows of -c_i
+    static constexpr int bytes = fold_max + 4;
 };
 // + alignment slack; rounded up past half of the SM's 228 KB so that only
 // one CTA is resident per SM (each CTA allocates all 512 TMEM columns)
@@ -328,10 +331,11 @@ __device__ __forceinline__ float bf16hi_to_f(uint32_t v) { return __uint_as_floa
 template <bool TF32>
 __global__ void __launch_bounds__(256)
 k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
-         uint8_t* __restrict__ img) {
+         uint8_t* __restrict__ img, uint32_t* __restrict__ wmax) {
     constexpr int TN = Tile<TF32>::TN;
     constexpr int PTS = TF32 ? 4 : 8;                    // points per 16-byte chunk
     const int64_t total = tiles * kRhs * 16;
+    uint32_t amax = 0;   // bits of max |W| seen by this thread (NaN bits order above inf)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int chunk = (int)(e % 16);                 // 16-byte chunk along K
@@ -344,6 +348,7 @@ k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
             for (int q = 0; q < 4; ++q) {
                 const int64_t j = t * TN + chunk * PTS + q;
                 const float v = (j < n && row < nrhs) ? __ldg(W + j * nrhs + row) : 0.0f;
+                amax = max(amax, __float_as_uint(v) & 0x7FFFFFFFu);
                 hi[q] = to_tf32(v);
                 lo[q] = to_tf32(v - __uint_as_float(hi[q]));
             }
@@ -355,6 +360,7 @@ k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
                 for (int h = 0; h < 2; ++h) {
                     const int64_t j = t * TN + chunk * PTS + 2 * q + h;
                     v[h] = (j < n && row < nrhs) ? __ldg(W + j * nrhs + row) : 0.0f;
+                    amax = max(amax, __float_as_uint(v[h]) & 0x7FFFFFFFu);
                 }
                 hi[q] = pack_bf16x2(v[0], v[1]);
                 lo[q] = pack_bf16x2(v[0] - bf16lo_to_f(hi[q]), v[1] - bf16hi_to_f(hi[q]));
@@ -366,6 +372,8 @@ k_prep_w(int64_t n, int nrhs, const float* __restrict__ W, int64_t tiles,
         // the lo row 64 + row: same (row % 8), 8 row groups (8 KB) further
         *reinterpret_cast<uint4*>(base + off + 8192) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
+    amax = __reduce_max_sync(0xffffffffu, amax);
+    if ((threadIdx.x & 31) == 0 && amax) atomicMax(wmax, amax);
 }
 
 // Order-independent float min/max through their sortable integer images.
@@ -459,8 +467,8 @@ template <bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                const float4* __restrict__ Yhat, const float4* __restrict__ centre,
-               const uint8_t* __restrict__ wimg, float sl2e, float* __restrict__ out,
-               uint32_t* __restrict__ err) {
+               const uint8_t* __restrict__ wimg, const uint32_t* __restrict__ wmax, float sl2e,
+               float* __restrict__ out, uint32_t* __restrict__ err) {
     // blockIdx.y selects a contiguous range of Y tiles; with gridDim.y == 2
     // the two partial sums are added into a zeroed output (0 + a + b is the
     // same in either order, so the result stays deterministic)
@@ -493,6 +501,7 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         }
         mbar_init(bar_acc, 1);
         *abort_flag = 0;
+        *(uint32_t*)(smem + SmemLayout::fold_max) = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kEpiWarps) {
@@ -559,8 +568,10 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             const uint64_t d0 = sw128_desc(sbase + SmemLayout::w + s * kStageBytes);
             if (elect_one_sync()) {
                 // 8 K steps of 32 bytes (16 bf16 or 8 tf32 points = 8 TMEM columns);
-                // split: D[:, 0:128] += (P_hi + P_lo) [W_hi | W_lo] as two N = 128
-                // MMAs (the extra P_lo W_lo term only adds accuracy)
+                // split: D[:, 0:128] += P_hi [W_hi | W_lo] (N = 128) and
+                // D[:, 0:64] += P_lo W_hi (N = 64): the three products.  A fourth,
+                // P_lo W_lo (2^-16 of the result), would cost a quarter more
+                // tensor work and, under the power cap, measurably lower clocks.
 #pragma unroll
                 for (int ks = 0; ks < 8; ++ks) {
                     const uint64_t bdesc = d0 + (uint64_t)(((ks / 4) * 16384 + (ks % 4) * 32) >> 4);
@@ -569,14 +580,14 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                     if (TF32) {
                         if (SPLIT) {
                             mma_ts_tf32(tmem + kColD, a_hi + acol, bdesc, kIdescTf32N128, acc0);
-                            mma_ts_tf32(tmem + kColD, a_lo + acol, bdesc, kIdescTf32N128, 1u);
+                            mma_ts_tf32(tmem + kColD, a_lo + acol, bdesc, kIdescTf32, 1u);
                         } else {
                             mma_ts_tf32(tmem + kColD, a_hi + acol, bdesc, kIdescTf32, acc0);
                         }
                     } else {
                         if (SPLIT) {
                             mma_ts(tmem + kColD, a_hi + acol, bdesc, kIdescBf16N128, acc0);
-                            mma_ts(tmem + kColD, a_lo + acol, bdesc, kIdescBf16N128, 1u);
+                            mma_ts(tmem + kColD, a_lo + acol, bdesc, kIdescBf16, 1u);
                         } else {
                             mma_ts(tmem + kColD, a_hi + acol, bdesc, kIdescBf16, acc0);
                         }
@@ -609,6 +620,21 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         }
         const uint64_t xa2 = f2pack(xa, xa), xb2 = f2pack(xb, xb), xc2 = f2pack(xc, xc);
         const uint64_t ci2 = f2pack(ci, ci);
+        // bf16 paths: fold the row term c_i out of the per-element exponent
+        // when the range allows.  P' = 2^(e - c_i) <= 2^(-c_i) (e <= 0), so
+        // sum_j P' |W_j| <= n max|W| 2^M with M the CTA's largest -c_i; the
+        // rows are scaled by 2^c_i after the MMAs.  The fold is taken only if
+        // that bound stays below 2^120 (and nothing is NaN), so the FP32
+        // accumulator cannot overflow where the unfolded form would not.
+        bool fold = false;
+        if (!TF32) {
+            uint32_t* fm = (uint32_t*)(smem + SmemLayout::fold_max);
+            atomicMax(fm, __float_as_uint(row0 + i < m ? -ci : 0.0f));   // -ci >= 0 (or NaN)
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");   // epilogue warps
+            const float M = __uint_as_float(*(volatile uint32_t*)fm);
+            const float wm = __uint_as_float(__ldg(wmax));
+            fold = M + log2f(wm) + log2f((float)total_tiles * Tile<TF32>::TN) < 120.0f;
+        }
         // bf16 paths: thread (g4, c4) = (lane / 4, lane % 4) evaluates rows
         // 8 r + g4 (r = 0..3) of its quadrant at column quads c4, so one
         // yhat load serves four rows (the 16x256b TMEM store layout)
@@ -633,19 +659,19 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
                 xq[r][3] = f2pack(ck, ck);
             }
         }
+        // the tile loop, compiled with and without the fold
+        auto tile_loop = [&](auto fold_c) {
+        constexpr bool FOLD = decltype(fold_c)::value;
         // ring positions and phase parities kept incrementally: a 64-bit
         // division per tile costs ~10% of the epilogue's issue slots
         int b = 0, st = 0;
         uint32_t pround = 0, sround = 0;   // (t / kPBufs) & 1, (t / kFwdStages) & 1
-        for (int64_t t = 0; t < tiles; ++t) {
-            if (t >= kPBufs) {
-                const bool ok = mbar_wait(bar_pempty + 8 * b, pround ^ 1u, abort_flag, err);
-                if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
-            }
-            {
-                const bool ok = mbar_wait(bar_full + 8 * st, sround, abort_flag, err);
-                if (!__all_sync(0xffffffffu, ok)) break;
-            }
+        const int ntiles = (int)tiles;
+        for (int t = 0; t < ntiles; ++t) {
+            bool ok = true;
+            if (t >= kPBufs) ok = mbar_wait(bar_pempty + 8 * b, pround ^ 1u, abort_flag, err);
+            ok = ok && mbar_wait(bar_full + 8 * st, sround, abort_flag, err);
+            if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.st needs the whole warp
             tc_fence_after();
             // yhat of this tile, read with explicit shared loads (a generic
             // pointer here would send every read down the global-load path)
@@ -700,7 +726,7 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
 #pragma unroll
                         for (int jp = 0; jp < 2; ++jp) {
                             const float4 A = jp ? Ao : Ae, B = jp ? Bo : Be;
-                            uint64_t e = add2(f2pack(B.z, B.w), xq[r][3]);
+                            uint64_t e = FOLD ? f2pack(B.z, B.w) : add2(f2pack(B.z, B.w), xq[r][3]);
                             e = fma2(xq[r][2], f2pack(B.x, B.y), e);
                             e = fma2(xq[r][1], f2pack(A.z, A.w), e);
                             e = fma2(xq[r][0], f2pack(A.x, A.y), e);
@@ -740,6 +766,13 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             if (++b == kPBufs) { b = 0; pround ^= 1u; }
             if (++st == kFwdStages) { st = 0; sround ^= 1u; }
         }
+        };
+        if constexpr (!TF32) {
+            if (fold) tile_loop(std::true_type{});
+            else tile_loop(std::false_type{});
+        } else {
+            tile_loop(std::false_type{});
+        }
         // accumulator ready (or aborted: the wait is still bounded)
         bool ok = mbar_wait(bar_acc, 0, abort_flag, err);
         ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld needs the whole warp
@@ -758,6 +791,11 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
                         v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(u[q]));
+                }
+                if (fold) {   // the row term folded out of the exponent
+                    const float sc = ex2f_tc(ci);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) * sc);
                 }
                 if (row0 + i < m) {
 #pragma unroll
@@ -1200,11 +1238,13 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     float4* Yhat = (float4*)(wimg + (size_t)tiles * kImgBytes);
     float4* centre = Yhat + tiles * TN;
     uint32_t* bbox = (uint32_t*)(centre + 1);
+    uint32_t* wmax = bbox + 8;   // max |W| (float bits), in the workspace's slack
     const int64_t prep_items = tiles * kRhs * 16;
-    k_prep_w<TF32><<<(unsigned)((prep_items + 255) / 256 < 4096 ? (prep_items + 255) / 256 : 4096), 256,
-                     0, st>>>(n, nrhs, W, tiles, wimg);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
+    k_prep_w<TF32><<<(unsigned)((prep_items + 255) / 256 < 4096 ? (prep_items + 255) / 256 : 4096), 256,
+                     0, st>>>(n, nrhs, W, tiles, wimg, wmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bbox, 0xFF, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bbox + 4, 0x00, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     k_bbox<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(n, Y, bbox);
@@ -1227,7 +1267,7 @@ static cudaError_t launch_tc(int64_t m, int64_t n, const float4* X, const float4
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)mblocks, (unsigned)split);
     k_dense_tc_fwd<TF32, SPLIT><<<grid, kThreadsTC, kSmemBytes, st>>>(m, tiles, X, Yhat, centre, wimg,
-                                                                      sl2e, out, err);
+                                                                      wmax, sl2e, out, err);
     return cudaGetLastError();
 }
 
