@@ -191,6 +191,55 @@ def test_tensor_core_full_size_sampled_rows(ab, ctx):
     assert errs["bf16x3"] < errs["bf16"] and errs["tf32x3"] < errs["tf32"], errs
 
 
+def _fold_bound(X, Y, W, s, m_rows):
+    """Per 128-row block: M + log2 max|W| + log2 n_pad, the quantity the BF16
+    forward compares with 120 to fold the row term out of the exponent
+    (M = max over the block's rows of s log2(e) |x - c|^2, c = centre of Y's
+    bounding box)."""
+    c = 0.5 * (Y.min(axis=0).astype(np.float64) + Y.max(axis=0))
+    q = s * np.log2(np.e) * np.sum((X.astype(np.float64) - c) ** 2, axis=1)
+    npad = -(-Y.shape[0] // 128) * 128
+    extra = np.log2(np.abs(W).max()) + np.log2(npad)
+    return np.array([q[b:b + 128].max() + extra for b in range(0, m_rows, 128)])
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", TC_TOL), ("bf16", 1e-2)])
+def test_tensor_core_row_fold_both_ways(ab, ctx, prec, tol):
+    """BF16 paths: CTAs whose rows lie near the centre of Y fold the row term
+    out of the exponent, CTAs whose rows lie far from it keep the unfolded
+    exponent; both against the FP64 oracle.  Points fill a 20-wide cube
+    (l = 1) with X sorted by distance from the centre, so the first row
+    blocks fold and the last ones do not."""
+    d = synth.c4(m=1024, n=2048, nrhs=64, seed_offset=77, lengthscale=1.0)
+    X = (20.0 * d.X).astype(np.float32)
+    Y = (20.0 * d.Y).astype(np.float32)
+    X = X[np.argsort(np.sum((X - 10.0) ** 2, axis=1), kind="stable")]
+    bound = _fold_bound(X, Y, d.W, d.s, X.shape[0])
+    assert (bound < 119.0).any() and (bound > 121.0).any(), bound   # both kinds present
+    out = host(ab.ab_kernel_matvec(ctx, _dev4(X), _dev4(Y), dev(d.W), d.s, prec))
+    ab.ab_sync(ctx)
+    ref = dense.matvec(X, Y, d.W, d.s)
+    den = dense.matvec_abs(X, Y, d.W, d.s)
+    err = np.max(np.abs(out - ref) / den)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", TC_TOL), ("bf16", 1e-2)])
+def test_tensor_core_huge_weights_stay_unfolded(ab, ctx, prec, tol):
+    """|W| ~ 2^100: folding would risk the FP32 accumulator, so every CTA
+    keeps the unfolded exponent; the result still matches FP64."""
+    d = synth.c4(m=512, n=700, nrhs=64, seed_offset=78)
+    W = (d.W * np.float32(2.0 ** 100)).astype(np.float32)
+    assert (_fold_bound(d.X, d.Y, W, d.s, d.X.shape[0]) > 121.0).all()
+    out = host(ab.ab_kernel_matvec(ctx, _dev4(d.X), _dev4(d.Y), dev(W), d.s, prec))
+    ab.ab_sync(ctx)
+    assert np.all(np.isfinite(out))
+    ref = dense.matvec(d.X, d.Y, W, d.s)
+    den = dense.matvec_abs(d.X, d.Y, W, d.s)
+    err = np.max(np.abs(out - ref) / den)
+    assert err <= tol, err
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("m,n", [(3000, 2000), (129, 33), (1, 300)])
 def test_tensor_core_adjoint(ab, ctx, prec, m, n):
