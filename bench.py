@@ -1019,6 +1019,22 @@ def probe(spec):
         torch.cuda.synchronize()
         ctx.close()
         return
+    if kind == "bd":   # N steps of the 2-D Brownian-dynamics loop ('bd:N'; default 13)
+        w = synth.c5()
+        p = w.params
+        pos = torch.from_numpy(w.pos).cuda()
+        F = torch.empty_like(pos)
+        ctx = ab.Context(0)
+        dom = ab.Domain(2, w.periodic, w.radius)
+        prm = ab.OpParams(k=p["k"])
+        for t in range(int(items) if items else 13):
+            ab.ab_build(ctx, dom, pos)
+            ab.ab_pair_sum(ctx, "soft", prm, out=F)
+            ab.ab_bd_step(ctx, dom, pos, F, p["dt"], p["D"], p["seed"], t)
+        ab.ab_sync(ctx)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
     if kind != "dense":
         raise SystemExit(f"unknown probe {spec!r}")
     d = synth.c4()
@@ -1051,7 +1067,8 @@ def main():
     ap.add_argument("--probe", default=None,
                     help="profiling aid: 'dense:bf16x3,tf32x3' runs one full-size dense call "
                          "per listed precision, 'c3' or 'c3:N' one clustered build, forward, "
-                         "adjoint and value-and-gradient, and exits (no timing, no JSON)")
+                         "adjoint and value-and-gradient, 'bd:N' N steps of the 2-D Brownian-"
+                         "dynamics loop, and exits (no timing, no JSON)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
