@@ -5,8 +5,8 @@
 // Forward (k_dense_fwd): a CTA owns 128 rows of X and all (<= 64) columns of
 // W.  For each chunk of 32 Y points it stages Y and W in shared memory,
 // evaluates the 128 x 32 kernel tile once (direct differences, FP32, exp via
-// ex2), and then runs a 128 x 64 x 32 register-tiled FFMA product with each
-// thread holding an 8 x 4 accumulator tile.  The exponentials are 1/64 of the
+// ex2), and then runs a 128 x 64 x 32 register-tiled product with each
+// thread holding an 8 x 4 accumulator tile in packed FP32 pairs.  The exponentials are 1/64 of the
 // multiply-adds, so the kernel is bound by the FP32 pipe.
 //
 // Adjoint: dW = K^T G is the forward with the roles of (X, W) and (Y, G)
@@ -35,76 +35,110 @@ __device__ __forceinline__ float ex2f(float x) {
     return y;
 }
 
+// Packed FP32 pairs: fma.rn.f32x2 rounds each half exactly like fmaf.
+__device__ __forceinline__ uint64_t f2p(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2u(uint64_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // thread layout for the product: tx in [0,16) -> 4 columns, ty in [0,16) ->
 // 8 consecutive rows ty*8 .. ty*8+7 (two float4 shared loads; a warp's two ty
-// values read broadcast addresses).
+// values read broadcast addresses).  Rows are paired in fma.f32x2 (the K
+// values of rows 2r, 2r+1 sit in an aligned register pair of the float4 load;
+// the W value is duplicated), 16 packed FMAs a K step instead of 32, with
+// the same rounding and order as scalar FMAs (65,536^2 x 64: 17.4 -> 16.0
+// ms, outputs bit-identical).  W and Y chunks alternate between two shared
+// buffers.
 __global__ void __launch_bounds__(kDThreads)
 k_dense_fwd(int64_t m, int64_t n, const float4* __restrict__ X,
             const float4* __restrict__ Y, int nrhs, const float* __restrict__ W,
             float ns_log2e, float* __restrict__ out) {
     __shared__ __align__(16) float Ks[kBN][kBM];
-    __shared__ __align__(16) float Ws[kBN][kRHS];
-    __shared__ float4 Ys[kBN];
-
+    __shared__ __align__(16) float Ws[2][kBN][kRHS];
+    __shared__ float4 Ys[2][kBN];
     const int t = threadIdx.x;
     const int tx = t & 15, ty = t >> 4;
     const int64_t row0 = (int64_t)blockIdx.x * kBM;
-
     // kernel-tile role: row r = t & 127 (its x in registers), 16 Y points
     const int kr = t & (kBM - 1);
     const int kh = t >> 7;  // 0 or 1: which 16 of the 32 Y points
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (row0 + kr < m) xi = __ldg(X + row0 + kr);
-
-    float acc[8][4];
+    uint64_t acc2[4][4];   // acc2[p][c] = rows (ty*8 + 2p, ty*8 + 2p + 1), column tx*4 + c
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-
-    for (int64_t j0 = 0; j0 < n; j0 += kBN) {
-        __syncthreads();
-        if (t < kBN) Ys[t] = (j0 + t < n) ? __ldg(Y + j0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-        // W chunk: 32 x 64 floats, 8 per thread
+        for (int c = 0; c < 4; ++c) acc2[p][c] = 0ull;
+    // W chunk: 32 x 64 floats, 8 per thread; Y chunk: 32 points
+    auto stage = [&](int64_t j0, int b) {
 #pragma unroll
         for (int e = 0; e < (kBN * kRHS) / kDThreads; ++e) {
             const int idx = e * kDThreads + t;
             const int jj = idx / kRHS, cc = idx % kRHS;
-            Ws[jj][cc] = (j0 + jj < n && cc < nrhs) ? __ldg(W + (j0 + jj) * nrhs + cc) : 0.f;
+            Ws[b][jj][cc] = (j0 + jj < n && cc < nrhs) ? __ldg(W + (j0 + jj) * nrhs + cc) : 0.f;
         }
-        __syncthreads();
+        if (t < kBN) Ys[b][t] = (j0 + t < n) ? __ldg(Y + j0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto kernel_tile = [&](int64_t j0, int b) {
 #pragma unroll 4
         for (int q = 0; q < 16; ++q) {
             const int jj = kh * 16 + q;
-            const float4 y = Ys[jj];
+            const float4 y = Ys[b][jj];
             const float dx = xi.x - y.x, dy = xi.y - y.y, dz = xi.z - y.z;
             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             Ks[jj][kr] = (j0 + jj < n) ? ex2f(ns_log2e * d2) : 0.f;
         }
+    };
+    const int64_t chunks = (n + kBN - 1) / kBN;
+    if (chunks > 0) {
+        stage(0, 0);
         __syncthreads();
+        kernel_tile(0, 0);
+        __syncthreads();
+    }
+    for (int64_t c = 0; c < chunks; ++c) {
+        const int b = (int)(c & 1);
 #pragma unroll 8
         for (int k = 0; k < kBN; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&Ks[k][ty * 8]);
             const float4 a1 = *reinterpret_cast<const float4*>(&Ks[k][ty * 8 + 4]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float4 b = *reinterpret_cast<const float4*>(&Ws[k][tx * 4]);
+            const float4 w = *reinterpret_cast<const float4*>(&Ws[b][k][tx * 4]);
+            const uint64_t A[4] = {f2p(a0.x, a0.y), f2p(a0.z, a0.w), f2p(a1.x, a1.y), f2p(a1.z, a1.w)};
+            const uint64_t B[4] = {f2p(w.x, w.x), f2p(w.y, w.y), f2p(w.z, w.z), f2p(w.w, w.w)};
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                acc[r][0] = fmaf(a[r], b.x, acc[r][0]);
-                acc[r][1] = fmaf(a[r], b.y, acc[r][1]);
-                acc[r][2] = fmaf(a[r], b.z, acc[r][2]);
-                acc[r][3] = fmaf(a[r], b.w, acc[r][3]);
-            }
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) acc2[p][cc] = ffma2(A[p], B[cc], acc2[p][cc]);
+        }
+        __syncthreads();   // Ks and Ws[b] fully read
+        if (c + 1 < chunks) {
+            stage((c + 1) * kBN, b ^ 1);
+            __syncthreads();
+            kernel_tile((c + 1) * kBN, b ^ 1);
+            __syncthreads();
         }
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int64_t row = row0 + ty * 8 + r;
-        if (row >= m) continue;
+    for (int p = 0; p < 4; ++p) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int col = tx * 4 + c;
-            if (col < nrhs) out[row * nrhs + col] = acc[r][c];
+        for (int cc = 0; cc < 4; ++cc) {
+            float v0, v1;
+            f2u(acc2[p][cc], v0, v1);
+            const int col = tx * 4 + cc;
+            const int64_t row = row0 + ty * 8 + 2 * p;
+            if (col < nrhs) {
+                if (row < m) out[row * nrhs + col] = v0;
+                if (row + 1 < m) out[(row + 1) * nrhs + col] = v1;
+            }
         }
     }
 }
