@@ -21,8 +21,10 @@
 // W is prepared once per call (k_prep_w): split into bf16 hi/lo and laid out
 // tile by tile in exactly the shared-memory image the MMA reads (K-major,
 // 128-byte swizzle), so each tile arrives by one contiguous bulk copy.
-// Three P buffers let the epilogue run up to two tiles ahead of the MMAs.  The exponentials (MUFU) and the split are the bound, as in
-// a softmax-free attention forward.
+// Three P buffers let the epilogue run up to two tiles ahead of the MMAs.
+// The bound is the epilogue's instruction stream (exponent, ex2 and the
+// hi/lo split: about 5.5 warp instructions per element), with the MMAs
+// overlapped behind it; on the split paths the power cap sets the clock.
 //
 // Every wait is bounded: a role that waits longer than kWaitLimitNs raises
 // the CTA's abort flag and the device error word, every role leaves its loop,
