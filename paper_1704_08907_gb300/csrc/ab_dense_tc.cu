@@ -644,14 +644,14 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
         }
         const uint64_t xa2 = f2pack(xa, xa), xb2 = f2pack(xb, xb), xc2 = f2pack(xc, xc);
         const uint64_t ci2 = f2pack(ci, ci);
-        // bf16 paths: fold the row term c_i out of the per-element exponent
-        // when the range allows.  P' = 2^(e - c_i) <= 2^(-c_i) (e <= 0), so
+        // Fold the row term c_i out of the per-element exponent when the
+        // range allows.  P' = 2^(e - c_i) <= 2^(-c_i) (e <= 0), so
         // sum_j P' |W_j| <= n max|W| 2^M with M the CTA's largest -c_i; the
         // rows are scaled by 2^c_i after the MMAs.  The fold is taken only if
         // that bound stays below 2^120 (and nothing is NaN), so the FP32
         // accumulator cannot overflow where the unfolded form would not.
-        bool fold = false;
-        if (!TF32) {
+        bool fold;
+        {
             uint32_t* fm = (uint32_t*)(smem + SmemLayout::fold_max);
             atomicMax(fm, __float_as_uint(row0 + i < m ? -ci : 0.0f));   // -ci >= 0 (or NaN)
             asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");   // epilogue warps
@@ -702,10 +702,10 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             const uint32_t yt = sbase + SmemLayout::w + st * kStageBytes + kImgBytes +
                                 part * kColsPerWarp * 16;
             // exponent of a column pair with packed FP32 pairs:
-            //   e = xa yx + (xb yy + (xc yz + (yw + ci)))
+            //   e = xa yx + (xb yy + (xc yz + (yw + ci)))  (+ ci dropped when folded)
             auto exponent2 = [&](int pair, float& e0, float& e1) {
                 const float4 A = lds128(yt + 32 * pair), B = lds128(yt + 32 * pair + 16);
-                uint64_t e = add2(f2pack(B.z, B.w), ci2);
+                uint64_t e = FOLD ? f2pack(B.z, B.w) : add2(f2pack(B.z, B.w), ci2);
                 e = fma2(xc2, f2pack(B.x, B.y), e);
                 e = fma2(xb2, f2pack(A.z, A.w), e);
                 e = fma2(xa2, f2pack(A.x, A.y), e);
@@ -791,12 +791,8 @@ k_dense_tc_fwd(int64_t m, int64_t total_tiles, const float4* __restrict__ X,
             if (++st == kFwdStages) { st = 0; sround ^= 1u; }
         }
         };
-        if constexpr (!TF32) {
-            if (fold) tile_loop(std::true_type{});
-            else tile_loop(std::false_type{});
-        } else {
-            tile_loop(std::false_type{});
-        }
+        if (fold) tile_loop(std::true_type{});
+        else tile_loop(std::false_type{});
         // accumulator ready (or aborted: the wait is still bounded)
         bool ok = mbar_wait(bar_acc, 0, abort_flag, err);
         ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld needs the whole warp

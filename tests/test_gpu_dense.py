@@ -191,21 +191,22 @@ def test_tensor_core_full_size_sampled_rows(ab, ctx):
     assert errs["bf16x3"] < errs["bf16"] and errs["tf32x3"] < errs["tf32"], errs
 
 
-def _fold_bound(X, Y, W, s, m_rows):
-    """Per 128-row block: M + log2 max|W| + log2 n_pad, the quantity the BF16
-    forward compares with 120 to fold the row term out of the exponent
+def _fold_bound(X, Y, W, s, m_rows, tile=128):
+    """Per 128-row block: M + log2 max|W| + log2 n_pad, the quantity the
+    tensor-core forward compares with 120 to fold the row term out of the exponent
     (M = max over the block's rows of s log2(e) |x - c|^2, c = centre of Y's
     bounding box)."""
     c = 0.5 * (Y.min(axis=0).astype(np.float64) + Y.max(axis=0))
     q = s * np.log2(np.e) * np.sum((X.astype(np.float64) - c) ** 2, axis=1)
-    npad = -(-Y.shape[0] // 128) * 128
+    npad = -(-Y.shape[0] // tile) * tile
     extra = np.log2(np.abs(W).max()) + np.log2(npad)
     return np.array([q[b:b + 128].max() + extra for b in range(0, m_rows, 128)])
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", TC_TOL), ("bf16", 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", TC_TOL), ("bf16", 1e-2), ("tf32x3", TC_TOL),
+                                      ("tf32", 1e-2)])
 def test_tensor_core_row_fold_both_ways(ab, ctx, prec, tol):
-    """BF16 paths: CTAs whose rows lie near the centre of Y fold the row term
+    """Tensor-core paths: CTAs whose rows lie near the centre of Y fold the row term
     out of the exponent, CTAs whose rows lie far from it keep the unfolded
     exponent; both against the FP64 oracle.  Points fill a 20-wide cube
     (l = 1) with X sorted by distance from the centre, so the first row
@@ -224,7 +225,8 @@ def test_tensor_core_row_fold_both_ways(ab, ctx, prec, tol):
     assert err <= tol, err
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", TC_TOL), ("bf16", 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", TC_TOL), ("bf16", 1e-2), ("tf32x3", TC_TOL),
+                                      ("tf32", 1e-2)])
 def test_tensor_core_huge_weights_stay_unfolded(ab, ctx, prec, tol):
     """|W| ~ 2^100: folding would risk the FP32 accumulator, so every CTA
     keeps the unfolded exponent; the result still matches FP64."""
