@@ -994,6 +994,52 @@ def oracle_sample(w, nq, seed=17):
     return int(off[-1]), dt, oracle.num_threads()
 
 
+def build_paths(reps=10):
+    """Median CUDA-event time of ab_build on each build path (counting sort as
+    a kernel sequence, as one cooperative launch, radix sort) for the
+    workloads' inputs, L2 flushed before every timed build."""
+    import torch
+    import paper_1704_08907_gb300 as ab
+    cases = {
+        "c2_1M_uniform_3d": (synth.c2(), 3),
+        "c3_16M_clustered_3d": (synth.c3(), 3),
+        "c5_4M_uniform_2d": (synth.c5(), 2),
+    }
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx = ab.Context(0)
+    res = {}
+    for name, (w, dim) in cases.items():
+        pos = torch.from_numpy(w.pos).cuda()
+        dom = ab.Domain(dim, w.periodic, w.radius)
+        row = {}
+        for path, label in ((ab.BUILD_SEQUENCE, "sequence"), (ab.BUILD_COOP, "coop"),
+                            (ab.BUILD_RADIX, "radix"), (ab.BUILD_AUTO, "auto")):
+            ab.ab_testing_build_path(ctx, path)
+            for _ in range(3):
+                ab.ab_build(ctx, dom, pos)
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ab.ab_build(ctx, dom, pos)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ab.ab_sync(ctx)
+            row[label] = round(float(np.median(ts)) * 1e3, 1)
+        _, ncells = ab.ab_cell_shape(ctx)
+        row["n"] = w.n
+        row["n_cells"] = ncells
+        row["unit"] = "us"
+        res[name] = row
+        del pos
+    ab.ab_testing_build_path(ctx, ab.BUILD_AUTO)
+    ctx.close()
+    return res
+
+
 def probe(spec):
     """One call per listed item, for ncu captures of a single kernel."""
     import torch
@@ -1035,6 +1081,9 @@ def probe(spec):
         torch.cuda.synchronize()
         ctx.close()
         return
+    if kind == "build-paths":   # time every build path on the workloads' inputs
+        print(json.dumps(build_paths(int(items) if items else 10)))
+        return
     if kind != "dense":
         raise SystemExit(f"unknown probe {spec!r}")
     d = synth.c4()
@@ -1068,7 +1117,9 @@ def main():
                     help="profiling aid: 'dense:bf16x3,tf32x3' runs one full-size dense call "
                          "per listed precision, 'c3' or 'c3:N' one clustered build, forward, "
                          "adjoint and value-and-gradient, 'bd:N' N steps of the 2-D Brownian-"
-                         "dynamics loop, and exits (no timing, no JSON)")
+                         "dynamics loop, and exits (no timing, no JSON); 'build-paths' or "
+                         "'build-paths:R' prints the median time of R builds on each "
+                         "build path for the 1M, clustered 16.7M and 2-D 4M inputs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

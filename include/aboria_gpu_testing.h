@@ -35,24 +35,32 @@ ab_status ab_testing_scan_timeout(ab_ctx* ctx, int64_t items, int32_t skip_tile,
  * time differ.  Errors: AB_ERR_INVALID_ARG. */
 ab_status ab_testing_cell_table(ab_ctx* ctx, int32_t mode);
 
-/* Select how the following ab_build calls run: single_launch = 1 (the
- * default) builds the cell list in one cooperative launch whose phases are
- * separated by bounded grid-wide barriers (above 2^21 particles with a dense
- * table the kernel sequence is used, being faster there); 0 always runs the
- * same counting sort as a sequence of kernels (a compact table is always
- * built in one launch).  Both give the same cell list bit for bit.
+/* Select how the following ab_build calls run:
+ *   0  the counting sort as a sequence of kernels (hash + atomic histogram,
+ *      scan, scatter, stable finalize); a compact table has no sequence form
+ *      and is built as in 1;
+ *   1  the same counting sort in one cooperative launch whose phases are
+ *      separated by bounded grid-wide barriers (above 2^21 particles with a
+ *      dense table the kernel sequence is used);
+ *   2  the stable radix sort of the cell ids (no per-particle global
+ *      atomic; see ab_build);
+ *   3  the automatic choice (the default).
+ * Every path gives the same cell list bit for bit.
  * Errors: AB_ERR_INVALID_ARG. */
-ab_status ab_testing_build_path(ab_ctx* ctx, int32_t single_launch);
+ab_status ab_testing_build_path(ab_ctx* ctx, int32_t path);
 
-/* Make the next single-launch ab_build exercise its barrier timeout: block
- * `skip_block` (clamped to none if the grid is smaller) never arrives at the
- * first grid barrier, so every other block's wait there gives up after
- * `limit_ns` nanoseconds (0 < limit_ns <= 2e9) and records AB_ERR_TIMEOUT in
- * the context's error word; all later waits of that launch are bounded the
- * same way, so the launch ends after at most five limits.  The cell list it
- * leaves is garbage; the following ab_sync() returns AB_ERR_TIMEOUT and a
- * new ab_build restores a valid cell list.  Applies to one build only.
- * Errors: AB_ERR_INVALID_ARG. */
+/* Make the next ab_build exercise its bounded wait.  On the cooperative
+ * launch, block `skip_block` (clamped to none if the grid is smaller) never
+ * arrives at the first grid barrier, so every other block's wait there gives
+ * up after `limit_ns` nanoseconds (0 < limit_ns <= 2e9); all later waits of
+ * that launch are bounded the same way, so it ends after at most five
+ * limits.  On the radix sort, tile `skip_block` of the scan of the first
+ * digit's counts never publishes its sum, so the look-back of the scan tiles
+ * after it gives up after `limit_ns`.  Either way the timeout is recorded as AB_ERR_TIMEOUT in the
+ * context's error word, every access stays inside the library's buffers, the
+ * cell list left behind is garbage, the following ab_sync() returns
+ * AB_ERR_TIMEOUT, and a new ab_build restores a valid cell list.  Applies to
+ * one build only.  Errors: AB_ERR_INVALID_ARG. */
 ab_status ab_testing_build_timeout(ab_ctx* ctx, int32_t skip_block, int64_t limit_ns);
 
 #ifdef __cplusplus

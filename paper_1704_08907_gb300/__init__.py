@@ -340,13 +340,20 @@ def ab_testing_cell_table(ctx: Context, mode: int):
     _check(_lib.ab_testing_cell_table(ctx.handle, int(mode)), ctx)
 
 
-def ab_testing_build_path(ctx: Context, single_launch: bool):
-    """Testing hook: one cooperative launch (True, default) or the kernel sequence."""
-    _check(_lib.ab_testing_build_path(ctx.handle, int(bool(single_launch))), ctx)
+BUILD_SEQUENCE, BUILD_COOP, BUILD_RADIX, BUILD_AUTO = range(4)
+
+
+def ab_testing_build_path(ctx: Context, path: int):
+    """Testing hook: how ab_build runs -- 0 the counting sort as a kernel
+    sequence, 1 the counting sort in one cooperative launch, 2 the radix
+    sort, 3 the automatic choice (the default)."""
+    _check(_lib.ab_testing_build_path(ctx.handle, int(path)), ctx)
 
 
 def ab_testing_build_timeout(ctx: Context, skip_block: int, limit_ns: int):
-    """Testing hook: the next single-launch build's first barrier misses a block."""
+    """Testing hook: in the next build, block `skip_block` never arrives at
+    the first barrier (radix sort: scan tile `skip_block` of the first digit's
+    counts never publishes its sum)."""
     _check(_lib.ab_testing_build_timeout(ctx.handle, int(skip_block), int(limit_ns)), ctx)
 
 

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libaboria_gpu.so")
-SOURCES = ["ab_api.cu", "ab_cells.cu", "ab_pairs.cu", "ab_dense.cu", "ab_dense_tc.cu", "ab_bd.cu",
+SOURCES = ["ab_api.cu", "ab_cells.cu", "ab_sort.cu", "ab_pairs.cu", "ab_dense.cu", "ab_dense_tc.cu", "ab_bd.cu",
            "ab_solve.cu"]
 HEADERS = [os.path.join(CSRC, "ab_internal.cuh"),
            os.path.join(ROOT, "include", "aboria_gpu.h"),

@@ -285,7 +285,8 @@ ab_status ab_destroy(ab_ctx* c) {
     cudaStreamSynchronize(c->stream);
     void* bufs[] = {c->cl.spos, c->cl.perm, c->cl.cell_rank, c->cl.tmp,
                     c->cl.cell_start, c->cl.occ, c->sc.sv, c->sc.scan_status, c->sc.scan_ticket,
-                    c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws, c->sc.coop};
+                    c->sc.partial, c->sc.counts, c->sc.dense_ws, c->sc.solve_ws, c->sc.coop,
+                    c->sc.rs_status, c->sc.rs_small};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -370,9 +371,30 @@ static ab_status build_impl(ab_ctx* c, const ab_domain* dom, int64_t n, const fl
     const size_t table = g.compact ? (size_t)n + 1 : (size_t)g.n_cells + 1;
     if ((e = grow(&cl.cell_start, &cl.cap_cells, table, c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ab_build (cell table)");
-    if (g.compact &&
+    // the radix build finds the occupied cells' offsets first, for the dense
+    // table too
+    const int path = c->build_opt.path == ab::kPathAuto ? ab::auto_build_path(n, g)
+                                                        : c->build_opt.path;
+    const bool radix = path == ab::kPathRadix && ab::radix_supported(n, g.n_cells);
+    if ((g.compact || radix) &&
         (e = grow(&cl.occ, &cl.cap_occ, (size_t)ab::occ_words(g.n_cells), c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ab_build (occupancy table)");
+    if (radix) {
+        uint64_t* before = c->sc.rs_status;
+        if ((e = grow(&c->sc.rs_status, &c->sc.cap_rs_status,
+                      ab::radix_status_words(n, g.n_cells), c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "ab_build (radix look-back words)");
+        if (c->sc.rs_status != before) c->sc.rs_epoch = 0;   // fresh memory: clear before use
+        if (!c->sc.rs_small) {
+            e = cudaMallocAsync((void**)&c->sc.rs_small, ab::radix_small_words() * sizeof(uint32_t),
+                                c->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                c->sc.rs_small = nullptr;
+                return cuda_fail(c, e, "ab_build (radix counts)");
+            }
+        }
+    }
     s = ensure_scan(c, g.n_cells + 1);
     if (s != AB_OK) return s;
     if (!c->sc.coop) {
@@ -840,9 +862,9 @@ ab_status ab_testing_cell_table(ab_ctx* c, int32_t mode) {
     return AB_OK;
 }
 
-ab_status ab_testing_build_path(ab_ctx* c, int32_t single_launch) {
-    if (!c || (single_launch != 0 && single_launch != 1)) return AB_ERR_INVALID_ARG;
-    c->build_opt.single_launch = single_launch != 0;
+ab_status ab_testing_build_path(ab_ctx* c, int32_t path) {
+    if (!c || path < ab::kPathSequence || path > ab::kPathAuto) return AB_ERR_INVALID_ARG;
+    c->build_opt.path = path;
     return AB_OK;
 }
 

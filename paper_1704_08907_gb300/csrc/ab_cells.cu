@@ -749,6 +749,17 @@ static int coop_grid(const void* fn, int64_t n, int64_t nc1) {
 
 size_t coop_scratch_words() { return 2 + 4096; }   // barrier words + block sums
 
+// The counting sort in one launch where the device allows it (the kernel
+// sequence above 2^21 particles with a dense table).  The radix sort of
+// ab_sort.cu gives the same cell list and is selected only on request: it
+// measured slower on every workload here (1M uniform points 98 vs 54 us,
+// 16.7M clustered 857-877 vs 844-857 us, 4M 2-D points 241 vs 168 us).
+int auto_build_path(int64_t n, const Geom& g) {
+    (void)n;
+    (void)g;
+    return kPathCoop;
+}
+
 cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
                          uint32_t* err, cudaStream_t st, const BuildOptions& opt) {
     const int64_t n = cl.n;
@@ -762,7 +773,10 @@ cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& s
     // the saved launches are worth (measured: 1M uniform points 53.9 vs
     // 56.4 us; 4M points in 2-D 176.8 vs 167.6 us).
     constexpr int64_t kSingleLaunchMaxN = int64_t(1) << 21;
-    if (sc.coop && (compact || (opt.single_launch && n <= kSingleLaunchMaxN))) {
+    const int path = opt.path == kPathAuto ? auto_build_path(n, cl.g) : opt.path;
+    if (path == kPathRadix && radix_supported(n, nc))
+        return launch_build_radix(cl, pos, packed, sc, err, st, opt);
+    if (sc.coop && (compact || (path != kPathSequence && n <= kSingleLaunchMaxN))) {
         const void* fn;
         if (compact) {
             if (cl.g.dim == 3) fn = packed ? (const void*)k_build_coop_compact<3, true> : (const void*)k_build_coop_compact<3, false>;

@@ -84,22 +84,42 @@ struct Scratch {
     uint8_t* solve_ws = nullptr;      // CG vectors and scalars
     size_t cap_solve_ws = 0;
     uint32_t* coop = nullptr;         // cooperative build: barrier words + block sums
+    uint64_t* rs_status = nullptr;    // radix build: look-back words (epoch-tagged)
+    size_t cap_rs_status = 0;
+    uint32_t* rs_small = nullptr;     // radix build: tickets + digit counts
+    uint32_t rs_epoch = 0;            // next look-back epoch (0: clear rs_status first)
 };
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 
 // ab_cells.cu
-// How ab_build runs: one cooperative launch (default) or the kernel
-// sequence; the last two fields are testing hooks of the bounded barrier wait.
+// How ab_build runs (see ab_testing_build_path): the counting sort as a
+// kernel sequence, the counting sort in one cooperative launch, the radix
+// sort of ab_sort.cu, or the automatic choice; the last two fields are
+// testing hooks of the bounded waits.
+enum BuildPath : int { kPathSequence = 0, kPathCoop = 1, kPathRadix = 2, kPathAuto = 3 };
 struct BuildOptions {
-    bool single_launch = true;
-    int skip_block = -1;          // a block that never arrives at the first barrier
-    long long limit_ns = 0;       // barrier wait limit (0: one second)
+    int path = kPathAuto;
+    int skip_block = -1;          // a block (tile) that never arrives (publishes)
+    long long limit_ns = 0;       // wait limit (0: one second)
 };
+// The path an automatic build takes for n particles and this geometry.
+AB_HIDDEN int auto_build_path(int64_t n, const Geom& g);
 AB_HIDDEN cudaError_t launch_build(CellList& cl, const float* pos, bool packed, Scratch& sc,
                                    uint32_t* err, cudaStream_t st, const BuildOptions& opt);
 // words of Scratch::coop (allocated once per context)
 AB_HIDDEN size_t coop_scratch_words();
+
+// ab_sort.cu: the cell list by a stable radix sort of the cell ids (the same
+// cell list as launch_build, bit for bit).  Needs cl.occ for the dense table
+// too, Scratch::rs_status of radix_status_words() and Scratch::rs_small of
+// radix_small_words().
+AB_HIDDEN bool radix_supported(int64_t n, int64_t n_cells);
+AB_HIDDEN size_t radix_status_words(int64_t n, int64_t n_cells);
+AB_HIDDEN size_t radix_small_words();
+AB_HIDDEN cudaError_t launch_build_radix(CellList& cl, const float* pos, bool packed,
+                                         Scratch& sc, uint32_t* err, cudaStream_t st,
+                                         const BuildOptions& opt);
 // The dense offsets of a compact cell list: out[c] = first slot of cell c,
 // c = 0 .. n_cells (device uint32[n_cells + 1]).
 AB_HIDDEN cudaError_t launch_expand_cells(const CellList& cl, uint32_t* out, cudaStream_t st);
