@@ -53,8 +53,8 @@ ab_status ab_testing_build_path(ab_ctx* ctx, int32_t path);
  * launch, block `skip_block` (clamped to none if the grid is smaller) never
  * arrives at the first grid barrier, so every other block's wait there gives
  * up after `limit_ns` nanoseconds (0 < limit_ns <= 2e9); all later waits of
- * that launch are bounded the same way, so it ends after at most five
- * limits.  On the radix sort, tile `skip_block` of the scan of the first
+ * that launch are bounded the same way, so it ends after at most one limit
+ * per grid barrier (five for a dense table, eight for a compact one).  On the radix sort, tile `skip_block` of the scan of the first
  * digit's counts never publishes its sum, so the look-back of the scan tiles
  * after it gives up after `limit_ns`.  Either way the timeout is recorded as AB_ERR_TIMEOUT in the
  * context's error word, every access stays inside the library's buffers, the
