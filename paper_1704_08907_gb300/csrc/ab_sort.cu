@@ -6,20 +6,22 @@
 // its histogram (and, for the compacted table, one more for the occupancy
 // bits); on large and clustered inputs those atomics are most of the build.
 // This build takes no per-particle global atomic:
-//   1. keys: each particle's cell id (the counting sort's hash), and the
-//      counts of every digit value, per block in shared memory, added to the
-//      global counts once per block and bin;
-//   2. one pass per digit of up to 10 bits, least significant first.  A tile
-//      of 4096 keys ranks its keys by digit in shared memory -- stably: each
-//      warp takes its 512 keys in order, 32 at a time, and __match_any_sync
-//      groups equal digits -- finds the global slot of its first key of each
-//      digit by decoupled look-back over the tiles before it (Merrill &
-//      Garland, 2016), and writes keys and original indices out in digit
-//      order.  The last pass writes the permutation and gathers the
-//      positions into sorted order.  Every pass is stable and the first one
-//      starts from original order, so the particles of a cell keep
-//      increasing original index: the sorted order, and hence the cell list,
-//      is the counting sort's bit for bit;
+//   1. keys: each particle's cell id (the counting sort's hash), and each
+//      tile's count of the first digit (tile = 4096 keys, shared-memory
+//      counts), stored bin-major: counts[d * tiles + t];
+//   2. one pass per digit of up to 10 bits, least significant first: the
+//      tiles' counts of the digit (from the previous pass's output), one
+//      exclusive scan of the bin-major counts -- a single-pass scan with
+//      decoupled look-back (Merrill & Garland, 2016) -- which gives every
+//      tile the global slot of its first key of each digit, then the pass
+//      itself: each warp ranks its 256 keys in order, 32 at a time, equal
+//      digits grouped by one ballot per digit bit (stable), the tile stages
+//      its keys in digit order in shared memory and writes each digit's run
+//      to consecutive global slots.  The last pass writes the permutation
+//      and gathers the positions into sorted order.  Every pass is stable
+//      and the first starts from original order, so the particles of a cell
+//      keep increasing original index: the sorted order, and hence the cell
+//      list, is the counting sort's bit for bit;
 //   3. cell boundaries: a sorted particle whose key differs from its
 //      predecessor's starts an occupied cell; its rank among the boundaries
 //      (a look-back scan) indexes the offsets of the occupied cells, and its
@@ -30,9 +32,10 @@
 // Look-back state words carry a 30-bit epoch, unique to one launch, so the
 // status array needs no clearing between launches.  Every wait on another
 // tile is bounded by a wall-clock limit after which the tile latches
-// DEVERR_SCAN_TIMEOUT and carries on (the results are then garbage, but every
-// tile terminates).  Tiles take increasing ids from a ticket counter, so a
-// tile only ever waits on tiles that are already running.
+// DEVERR_SCAN_TIMEOUT and carries on (the results are then garbage, but
+// every access is checked to stay in its array and every tile terminates).
+// Scan tiles take increasing ids from a ticket counter, so a tile only ever
+// waits on tiles that are already running.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
