@@ -537,6 +537,79 @@ __device__ __forceinline__ void coop_finalize(const CoopArgs& a, int64_t tid, in
     }
 }
 
+// Compact index of dense cell c: its rank among the occupied cells.
+__device__ __forceinline__ uint32_t compact_index(const uint4* occ, uint32_t c) {
+    const uint4 q = __ldcg(occ + (c >> 6));
+    const uint64_t bits = ((uint64_t)q.y << 32) | q.x;
+    return q.z + (uint32_t)__popcll(bits & ((1ull << (c & 63u)) - 1ull));
+}
+
+// Compact table: scatter the original index (4 bytes) into the particle's
+// unordered slot.  The 4-byte slot array stays in L2 on large inputs where
+// the 8-byte (index, cell) records of coop_scatter do not.
+__device__ __forceinline__ void coop_scatter_idx(const CoopArgs& a, uint32_t* slot_idx,
+                                                 int64_t tid, int64_t nthreads) {
+    const int64_t n = a.n;
+    for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
+        uint2 kr[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            kr[u] = i < n ? ldcg_u2(a.cell_rank + i) : make_uint2(0u, 0u);
+        }
+        uint32_t st[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            st[u] = i0 + u * nthreads < n ? ldcg_u32(a.cell_start + kr[u].x) : 0u;
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t i = i0 + u * nthreads;
+            if (i < n) slot_idx[st[u] + kr[u].y] = (uint32_t)i;
+        }
+    }
+}
+
+// Compact table: the stable finalize from 4-byte slots.  The slot's cell is
+// recomputed from the gathered position (the hash's expression, then the
+// compact index), so the slot needs to carry only the original index.
+template <int DIM, bool PACKED>
+__device__ __forceinline__ void coop_finalize_idx(const CoopArgs& a, const uint32_t* slot_idx,
+                                                  int64_t tid, int64_t nthreads) {
+    const int64_t n = a.n;
+    for (int64_t s0 = tid; s0 < n; s0 += nthreads * kCoopIlp) {
+        uint32_t p[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const int64_t s = s0 + u * nthreads;
+            p[u] = s < n ? ldcg_u32(slot_idx + s) : 0u;
+        }
+        float4 q[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u)
+            q[u] = s0 + u * nthreads < n ? load_pos<DIM, PACKED>(a.pos, p[u])
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t k[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) k[u] = compact_index(a.occ, particle_cell<DIM, PACKED>(a, q[u]));
+        uint32_t lo[kCoopIlp], hi[kCoopIlp];
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            const bool live = s0 + u * nthreads < n;
+            lo[u] = live ? ldcg_u32(a.cell_start + k[u]) : 0u;
+            hi[u] = live ? ldcg_u32(a.cell_start + k[u] + 1) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kCoopIlp; ++u) {
+            if (s0 + u * nthreads >= n) continue;
+            uint32_t r = 0;
+            for (uint32_t t = lo[u]; t < hi[u]; ++t) r += (ldcg_u32(slot_idx + t) < p[u]) ? 1u : 0u;
+            const uint32_t d = lo[u] + r;
+            a.perm[d] = p[u];
+            a.spos[d] = make_float4(q[u].x, q[u].y, DIM == 3 ? q[u].z : 0.0f, 0.0f);
+        }
+    }
+}
+
 template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kCoopThreads, 1)
 k_build_coop(CoopArgs a) {
@@ -595,6 +668,10 @@ k_build_coop_compact(CoopArgs a) {
     for (int64_t c = tid; c <= n; c += nthreads) a.cell_start[c] = 0u;
     coop_barrier(a.bar, a.err, a.limit_ns, (int)blockIdx.x == a.skip_block);
 
+    // 4-byte per-particle words in the slot buffer: the cell id (P1 -> P3),
+    // then the original index of each unordered slot (P5 -> P6)
+    uint32_t* const idx32 = reinterpret_cast<uint32_t*>(a.tmp);
+
     // P1: cell hash; mark the cell occupied, keep its id
     for (int64_t i0 = tid; i0 < n; i0 += nthreads * kCoopIlp) {
         uint32_t c[kCoopIlp];
@@ -609,7 +686,7 @@ k_build_coop_compact(CoopArgs a) {
             const int64_t i = i0 + u * nthreads;
             if (i >= n) continue;
             atomicOr(reinterpret_cast<unsigned long long*>(a.occ + (c[u] >> 6)), 1ull << (c[u] & 63u));
-            a.cell_rank[i] = make_uint2(c[u], 0u);
+            idx32[i] = c[u];
         }
     }
     coop_barrier(a.bar, a.err, a.limit_ns);
@@ -648,14 +725,10 @@ k_build_coop_compact(CoopArgs a) {
 #pragma unroll
         for (int u = 0; u < kCoopIlp; ++u) {
             const int64_t i = i0 + u * nthreads;
-            c[u] = i < n ? ldcg_u2(a.cell_rank + i).x : 0u;
+            c[u] = i < n ? ldcg_u32(idx32 + i) : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < kCoopIlp; ++u) {
-            const uint4 q = __ldcg(a.occ + (c[u] >> 6));
-            const uint64_t bits = ((uint64_t)q.y << 32) | q.x;
-            k[u] = q.z + (uint32_t)__popcll(bits & ((1ull << (c[u] & 63u)) - 1ull));
-        }
+        for (int u = 0; u < kCoopIlp; ++u) k[u] = compact_index(a.occ, c[u]);
 #pragma unroll
         for (int u = 0; u < kCoopIlp; ++u)
             if (i0 + u * nthreads < n) r[u] = atomicAdd(a.cell_start + k[u], 1u);
@@ -673,9 +746,9 @@ k_build_coop_compact(CoopArgs a) {
     coop_barrier(a.bar, a.err, a.limit_ns);
 
     // P5: scatter; P6: stable finalize (over compact indices)
-    coop_scatter(a, tid, nthreads);
+    coop_scatter_idx(a, idx32, tid, nthreads);
     coop_barrier(a.bar, a.err, a.limit_ns);
-    coop_finalize<DIM, PACKED>(a, tid, nthreads);
+    coop_finalize_idx<DIM, PACKED>(a, idx32, tid, nthreads);
 }
 
 // Dense offsets of a compact cell list (inspection and export).
