@@ -265,6 +265,10 @@ k_scan(const uint32_t* in, TOut* out, int64_t n, uint64_t* status,
 constexpr int kRedThreads = 1024;
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce_partials(const double* __restrict__ partial, int count, double* __restrict__ out) {
+    // launched as a programmatic dependent of the kernel that writes the
+    // partials: wait until that grid has finished and its writes are visible
+    // (returns at once without a prerequisite grid)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // fixed assignment and tree order: deterministic for a given count
     __shared__ double s[kRedThreads];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -800,8 +804,20 @@ cudaError_t launch_scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n,
 
 cudaError_t launch_reduce_partials(const double* partial, int count, double* out,
                                    cudaStream_t st) {
-    k_reduce_partials<<<1, kRedThreads, 0, st>>>(partial, count, out);
-    return cudaGetLastError();
+    // programmatic dependent launch: the one-block reduction is scheduled
+    // while the kernel before it runs its last wave (the pair kernels signal
+    // launch_dependents at their start) and waits in griddepcontrol.wait, so
+    // its launch latency is hidden
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kRedThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_reduce_partials, partial, count, out);
 }
 
 // Grid of the cooperative build: every block resident (one 1024-thread block

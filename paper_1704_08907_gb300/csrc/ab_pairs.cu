@@ -301,6 +301,13 @@ __device__ __forceinline__ void visit_pairs(const PairParams& P, uint32_t s,
     });
 }
 
+// Lets a programmatic dependent launch of the partials' reduction begin
+// (its blocks then wait for this grid to finish): called at the start of
+// every kernel that writes block partials.
+__device__ __forceinline__ void allow_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
 // FP64 block sum of one value per thread into partial[blockIdx.x].
 template <int THREADS>
 __device__ __forceinline__ void block_partial(double v, double* partial) {
@@ -348,6 +355,7 @@ k_pair_fwd(PairParams P, PairOut o) {
 template <int DIM, int MODE, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd_q(PairParams P, PairOut o) {
+    allow_dependents();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -411,6 +419,7 @@ k_pair_fwd_q(PairParams P, PairOut o) {
 template <int DIM, int MODE, int OP, bool VALUE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_bwd(PairParams P, PairOut o) {
+    allow_dependents();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -472,6 +481,7 @@ k_pair_bwd(PairParams P, PairOut o) {
 template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_lj_eg(PairParams P, PairOut o) {
+    allow_dependents();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
