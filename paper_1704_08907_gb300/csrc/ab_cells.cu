@@ -617,6 +617,9 @@ __device__ __forceinline__ void coop_finalize_idx(const CoopArgs& a, const uint3
 template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kCoopThreads, 1)
 k_build_coop(CoopArgs a) {
+    // the pair kernel that follows may be scheduled now (it waits for this
+    // grid to finish before reading anything)
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_red[32];
     const int64_t n = a.n;
@@ -660,6 +663,9 @@ k_build_coop(CoopArgs a) {
 template <int DIM, bool PACKED>
 __global__ void __launch_bounds__(kCoopThreads, 1)
 k_build_coop_compact(CoopArgs a) {
+    // the pair kernel that follows may be scheduled now (it waits for this
+    // grid to finish before reading anything)
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_red[32];
     const int64_t n = a.n;

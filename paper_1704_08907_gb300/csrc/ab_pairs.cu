@@ -308,6 +308,15 @@ __device__ __forceinline__ void allow_dependents() {
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// Every pair kernel is a programmatic dependent launch of the kernel before
+// it on the stream (normally the build): it may be scheduled while that
+// kernel finishes, and waits here, before its first global read, until that
+// grid has completed and its writes are visible.  Without a prerequisite
+// grid the wait returns at once.
+__device__ __forceinline__ void wait_prerequisite() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // FP64 block sum of one value per thread into partial[blockIdx.x].
 template <int THREADS>
 __device__ __forceinline__ void block_partial(double v, double* partial) {
@@ -330,6 +339,7 @@ __device__ __forceinline__ void block_partial(double v, double* partial) {
 template <int DIM, int MODE, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd(PairParams P, PairOut o) {
+    wait_prerequisite();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
@@ -356,6 +366,7 @@ template <int DIM, int MODE, int OP>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_fwd_q(PairParams P, PairOut o) {
     allow_dependents();
+    wait_prerequisite();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -420,6 +431,7 @@ template <int DIM, int MODE, int OP, bool VALUE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_bwd(PairParams P, PairOut o) {
     allow_dependents();
+    wait_prerequisite();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -482,6 +494,7 @@ template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_lj_eg(PairParams P, PairOut o) {
     allow_dependents();
+    wait_prerequisite();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     const bool live = s < P.n;
     const float4 pi = live ? __ldg(P.spos + s) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -519,6 +532,7 @@ k_pair_lj_eg(PairParams P, PairOut o) {
 template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
+    wait_prerequisite();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
@@ -531,6 +545,7 @@ k_pair_count(PairParams P, uint32_t* __restrict__ counts) {
 template <int DIM, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 8)
 k_pair_emit(PairParams P, const int64_t* __restrict__ offsets, int32_t* __restrict__ idx) {
+    wait_prerequisite();
     const uint32_t s = blockIdx.x * kPairThreads + threadIdx.x;
     if (s >= P.n) return;
     const float4 pi = __ldg(P.spos + s);
@@ -570,20 +585,39 @@ PairParams make_params(const CellList& cl, const ab_op_params& prm, const float2
 
 int pair_grid(int64_t n) { return (int)((n + kPairThreads - 1) / kPairThreads); }
 
+// Launch as a programmatic dependent of the previous kernel on the stream
+// (see wait_prerequisite).
+template <class... KArgs, class... Args>
+static cudaError_t pdl_launch(void (*kern)(KArgs...), int grid, int threads, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 #define COMMA_OP(x) , x
 
 #define AB_DISPATCH_DG(KERNEL, THREADS, OPARGS, ...)                                  \
     do {                                                                              \
         const int grid = (int)((cl.n + THREADS - 1) / THREADS);                       \
+        cudaError_t le_;                                                              \
         if (cl.g.dim == 3) {                                                          \
-            if (cl.g.general) KERNEL<3, kModeGeneral OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
-            else if (cl.g.compact) KERNEL<3, kModeCompact OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
-            else KERNEL<3, kModeFast OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);   \
+            if (cl.g.general) le_ = pdl_launch(KERNEL<3, kModeGeneral OPARGS>, grid, THREADS, st, __VA_ARGS__); \
+            else if (cl.g.compact) le_ = pdl_launch(KERNEL<3, kModeCompact OPARGS>, grid, THREADS, st, __VA_ARGS__); \
+            else le_ = pdl_launch(KERNEL<3, kModeFast OPARGS>, grid, THREADS, st, __VA_ARGS__); \
         } else {                                                                      \
-            if (cl.g.general) KERNEL<2, kModeGeneral OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
-            else if (cl.g.compact) KERNEL<2, kModeCompact OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__); \
-            else KERNEL<2, kModeFast OPARGS><<<grid, THREADS, 0, st>>>(__VA_ARGS__);   \
+            if (cl.g.general) le_ = pdl_launch(KERNEL<2, kModeGeneral OPARGS>, grid, THREADS, st, __VA_ARGS__); \
+            else if (cl.g.compact) le_ = pdl_launch(KERNEL<2, kModeCompact OPARGS>, grid, THREADS, st, __VA_ARGS__); \
+            else le_ = pdl_launch(KERNEL<2, kModeFast OPARGS>, grid, THREADS, st, __VA_ARGS__); \
         }                                                                             \
+        if (le_ != cudaSuccess) return le_;                                           \
     } while (0)
 
 cudaError_t launch_pair_fwd(const CellList& cl, ab_op op, const ab_op_params& prm,
