@@ -54,8 +54,8 @@ OPS_PER_PAIR_LJ_EG = 12
 # DRAM traffic of one k_pair_lj_eg<3,false> launch on this workload, from an
 # ncu --set full capture (dram__bytes_read.sum + dram__bytes_write.sum), valid
 # only for the kernel source it was taken on (None until captured).
-TRAFFIC_EG_BYTES = 35.44e6   # 29.21 MB read + 6.23 MB written
-TRAFFIC_SOURCE_SHA = "dc1b75420db3b9d5"
+TRAFFIC_EG_BYTES = 35.54e6   # 29.28 MB read + 6.26 MB written
+TRAFFIC_SOURCE_SHA = "3b686070cc13ccc9"
 
 
 def alu_peak(pk):
@@ -602,9 +602,9 @@ def oracle_sample_c3(w, nq, seed=23):
 # DRAM traffic of one k_pair_bwd<3,false,GAUSS> launch on the clustered
 # workload (ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the
 # kernel source whose hash is given (None until captured on that source).
-TRAFFIC_C3_BWD_BYTES = 942.77e6    # 550.10 MB read + 392.67 MB written (adjoint kernel)
-TRAFFIC_C3_VG_BYTES = 1129.02e6    # 611.89 MB read + 517.13 MB written (value and gradient)
-TRAFFIC_C3_SOURCE_SHA = "dc1b75420db3b9d5"
+TRAFFIC_C3_BWD_BYTES = 942.84e6    # 550.14 MB read + 392.70 MB written (adjoint kernel)
+TRAFFIC_C3_VG_BYTES = 1129.44e6    # 612.22 MB read + 517.22 MB written (value and gradient)
+TRAFFIC_C3_SOURCE_SHA = "3b686070cc13ccc9"
 
 
 def also_c3(reps=5, oracle_fraction=64):
